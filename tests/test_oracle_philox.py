@@ -1,0 +1,44 @@
+"""Statistical pins of the oracle's counter-based Gaussian signals (Section 2.2, Step 1)."""
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle.philox import forgy_draw, gaussian_columns, philox4x32_10
+
+
+def test_gaussian_moments_and_normality():
+    d = 64
+    r = gaussian_columns(12345, 20000, np.arange(8), d)
+    z = (r * np.sqrt(d)).ravel()
+    assert abs(z.mean()) < 4 / np.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 4 * np.sqrt(2.0 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    corr = np.corrcoef(r.T)
+    off = corr[~np.eye(8, dtype=bool)]
+    assert np.max(np.abs(off)) < 5 / np.sqrt(20000)
+
+
+def test_columns_are_keyed_independently():
+    full = gaussian_columns(7, 500, np.arange(10), 10)
+    part = gaussian_columns(7, 500, np.array([3, 9]), 10)
+    np.testing.assert_array_equal(part, full[:, [3, 9]])
+    other_seed = gaussian_columns(8, 500, np.array([3]), 10)
+    assert not np.allclose(other_seed[:, 0], full[:, 3])
+
+
+def test_uniform_bits_are_uniform():
+    x0, x1, x2, x3 = philox4x32_10(np.arange(100000), 0, 5, 0, 1, 2)
+    for x in (x0, x1, x2, x3):
+        u = x.astype(np.float64) / 2.0**32
+        assert stats.kstest(u, "uniform").pvalue > 1e-3
+    # the round function mixes all inputs: changing one counter word changes every output word
+    y = philox4x32_10(np.arange(1000), 0, 6, 0, 1, 2)
+    for a, b in zip((x0[:1000], x1[:1000], x2[:1000], x3[:1000]), y):
+        assert np.mean(a == b) < 0.01
+
+
+def test_forgy_draw_distinct_in_range():
+    idx = forgy_draw(99, 50, 50)
+    assert sorted(idx.tolist()) == list(range(50))
+    idx = forgy_draw(99, 10**6, 100)
+    assert idx.min() >= 0 and idx.max() < 10**6 and np.unique(idx).size == 100
