@@ -1,0 +1,229 @@
+/*
+ * csc.h -- C ABI of the GB300 (sm_103a) dynamic compressive spectral clustering library.
+ *
+ * Method: Martin, Loukas, Vandergheynst, "Fast Approximate Spectral Clustering for
+ * Dynamic Networks" (ICML 2017, arXiv:1706.03591).  The calls follow the paper's
+ * statement of the problem (Algorithm 1: a graph sequence G_t, the number of
+ * signals d, the reuse fraction p and k in; assignments X_t out):
+ *
+ *   csc_set_graph        G_t as CSR                                  Section 2.1, Section 4
+ *   csc_estimate_lambda_k  eigencount dichotomy for the cutoff       Section 3.3, Algorithm 1 step 1
+ *   csc_filter           Jackson-damped Chebyshev filtering of the    Section 2.2 Step 1, Section 3.3,
+ *                        new signals, eigencount check, refinement,   Eq. 6, Algorithm 1 steps 4-7
+ *                        splice into the feature matrix Theta_t
+ *   csc_cluster          row normalisation + k-means on Theta_t       Eq. 1, Eq. 5, Algorithm 1 step 8
+ *
+ * plus stateless-per-call building blocks used by tests and benchmarks
+ * (csc_signals, csc_cheb_filter, csc_kmeans) and host-only helpers that need
+ * no GPU (coefficients, eigencount from moments, the dichotomy).
+ *
+ * Conventions (every entry point):
+ *  - Returns a csc_status; no exception or abort crosses the ABI.  Details of the
+ *    last failure on a context are in csc_last_error(ctx).
+ *  - `where` arguments say where a caller pointer lives: CSC_HOST (pageable or
+ *    pinned host memory) or CSC_DEVICE (device memory of the context's device).
+ *  - The library owns every device buffer it allocates (graph copy, recursion
+ *    blocks, feature ring, k-means state).  Caller buffers are only read or
+ *    written during the call; output buffers are caller-owned.
+ *  - All device work runs on the stream given to csc_create (NULL = legacy
+ *    default stream).  Calls that return host values synchronise that stream.
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - Layouts are row-major: an n x c block with leading dimension ld has
+ *    element (i, v) at base[i*ld + v].
+ */
+#ifndef CSC_H
+#define CSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSC_ABI_VERSION 1
+
+typedef struct csc_ctx csc_ctx;
+
+typedef enum csc_status {
+  CSC_OK = 0,
+  CSC_EINVAL = 1,   /* invalid argument (sizes, pointers, malformed CSR, unknown enum) */
+  CSC_ENOMEM = 2,   /* a device or host allocation failed */
+  CSC_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+  CSC_ETIMEOUT = 4, /* a bounded device-side wait expired */
+  CSC_ESTATE = 5    /* call order: e.g. csc_filter before csc_set_graph */
+} csc_status;
+
+enum { CSC_HOST = 0, CSC_DEVICE = 1 };
+enum { CSC_F32 = 0, CSC_BF16 = 1 };
+
+typedef struct csc_opts {
+  int precision;    /* CSC_F32: signal block and features stored in float32.
+                       CSC_BF16: signal block R and row-normalised features stored in
+                       bfloat16; the recursion and accumulation stay float32 and the
+                       eigencount trace sums and centroid sums exact/float64. */
+  double count_tol; /* eigencount acceptance half-width tau; <= 0 selects
+                       max(0.5, 2 sqrt(2k/c)) for a block of c signals */
+  int max_bisect;   /* cap on eigencount evaluations of the dichotomy (default 30) */
+  int max_iter;     /* cap on Lloyd assignment passes (default 100) */
+  int col_tile;     /* column-tile width of the recursion: 0 = automatic, else one of
+                       8, 16, 32, 64, 128 */
+  int checked;      /* nonzero: validate the CSR on csc_set_graph (device input too) */
+  int timing;       /* nonzero: time the Chebyshev step launches with CUDA events on the
+                       context stream (read with csc_get_stats) */
+} csc_opts;
+
+/* Counters of a context (csc_get_stats). */
+typedef struct csc_stats {
+  int64_t launches;       /* kernels this library launched on the context */
+  int64_t step_launches;  /* general Chebyshev step launches bracketed by timing events */
+  double step_ms;         /* device time of those launches (ms), CUDA events on the context stream */
+  int64_t filter_passes;  /* recursion passes (one per column tile per filtering call) */
+  int64_t tile;           /* column-tile width of the last filtering pass */
+} csc_stats;
+
+/* ---------------------------------------------------------------- library */
+
+/* Fills *opts with the defaults listed in csc_opts. */
+void csc_default_opts(csc_opts* opts);
+/* Static string for a status code. */
+const char* csc_status_string(csc_status s);
+/* CSC_ABI_VERSION of the built library. */
+int csc_abi_version(void);
+
+/* Creates a context on the current CUDA device.  `cuda_stream` is a cudaStream_t
+ * (NULL = default stream).  opts may be NULL (defaults).  *out is owned by the
+ * caller and released with csc_destroy. */
+csc_status csc_create(csc_ctx** out, const csc_opts* opts, void* cuda_stream);
+/* Frees every device and host buffer of the context (synchronises its stream). */
+void csc_destroy(csc_ctx* ctx);
+/* Message of the last failure on ctx ("" if none).  Valid until the next call. */
+const char* csc_last_error(const csc_ctx* ctx);
+
+/* Copies the context counters into *out; reset != 0 zeroes them afterwards. */
+csc_status csc_get_stats(csc_ctx* ctx, csc_stats* out, int reset);
+
+/* ---------------------------------------------------------------- graph */
+
+/* Section 2.1: G = (V, E, W), simple, undirected, W_ij > 0, no self-loops.
+ * Loads snapshot G_t as symmetric CSR: row_ptr int64[n+1] (row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n] = nnz), col_idx int32[nnz] in [0, n), vals
+ * float32[nnz] edge weights or NULL for unit weights.  Both directions of every
+ * edge must be stored.  The data are copied (host->device or device->device);
+ * the caller keeps ownership.  Computes degrees and D^{-1/2} (0 for isolated
+ * nodes) of the normalized Laplacian L = I - D^{-1/2} W D^{-1/2}.
+ * n must equal the n of earlier snapshots on this context (fixed vertex set,
+ * Section 4) unless no snapshot has been filtered yet.
+ * Errors: CSC_EINVAL on bad sizes or (host input, or checked mode) malformed
+ * CSR; CSC_ENOMEM; CSC_ECUDA. */
+csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                         const int32_t* col_idx, const float* vals, int where);
+
+/* ---------------------------------------------------------------- host-only helpers (no GPU) */
+
+/* Section 3.3: coefficients a_0..a_m (a_out double[m+1]) of the order-m
+ * Jackson-damped Chebyshev approximation of 1[lambda <= lambda_c] on [0, 2],
+ * h(lambda) = sum_j a_j T_j(lambda - 1).  lambda_c is clamped to [0, 2].
+ * Errors: CSC_EINVAL if m < 0 or a_out is NULL. */
+csc_status csc_filter_coeffs(int m, double lambda_c, double* a_out);
+
+/* Default eigencount acceptance half-width max(0.5, 2 sqrt(2k/c)). */
+double csc_count_tolerance(int k, int c);
+
+/* Section 3.3 eigencount from the trace moments mu_l = tr(R^T T_l(L~) R),
+ * l = 0..2m (mu double[2m+1]): count = (d/c) sum_{i,j} a_i a_j (mu_{i+j} + mu_{|i-j|})/2
+ * = (d/c) ||h(L) R||_F^2 for c signals of variance 1/d. */
+csc_status csc_count_from_moments(int m, const double* mu, double lambda_c, int d, int c,
+                                  double* count_out);
+
+/* Algorithm 1 step 7 / Section 4.1 dichotomy on the moment-based eigencount:
+ * with lambda_prev < 0 bisect [0, 2]; else test lambda_prev, then grow a bracket
+ * 0.01 * 2^i toward k until the count crosses k, then bisect.  Accept when
+ * |count - k| <= tau; at most max_steps evaluations.  Outputs the cutoff, its
+ * count and the number of evaluations. */
+csc_status csc_lambda_search_moments(int m, const double* mu, int d, int c, int k, double tau,
+                                     double lambda_prev, int max_steps, double* lambda_out,
+                                     double* count_out, int* evals_out);
+
+/* ---------------------------------------------------------------- building blocks */
+
+/* Section 2.2 Step 1: the n x c block of i.i.d. N(0, 1/d) signals for global column
+ * ids col0 .. col0+c-1 (Philox-4x32-10 counter (row, column), key seed;
+ * Box-Muller).  out: dtype CSC_F32 or CSC_BF16, leading dimension ld >= c,
+ * caller-owned, host or device per `where`. */
+csc_status csc_signals(csc_ctx* ctx, uint64_t seed, int64_t n, int64_t col0, int c, int d,
+                       void* out, int dtype, int64_t ld, int where);
+
+/* Sections 2.2 and 3.3: Psi~ = h(L) R for the current graph, caller's signal block
+ * R (n x c, dtype CSC_F32 or CSC_BF16, leading dimension ldr, host or device per
+ * r_where), Jackson-damped order-m low-pass of cutoff lambda_c in [0, 2], m >= 1.
+ * psi_out: float32 n x c, leading dimension ldp >= c, host or device per
+ * psi_where (NULL: moments only).  mu_out: host double[2m+1] trace moments
+ * mu_l = tr(R^T T_l(L~) R) (NULL: not returned).  Does not touch the feature ring. */
+csc_status csc_cheb_filter(csc_ctx* ctx, int m, double lambda_c, const void* R, int r_dtype, int c,
+                           int64_t ldr, int r_where, float* psi_out, int64_t ldp, int psi_where,
+                           double* mu_out);
+
+/* Eq. 1-2 k-means (Lloyd) on caller features Y (n x d, dtype CSC_F32 or CSC_BF16,
+ * leading dimension ldy, host or device per y_where), used as given (no row
+ * normalisation).  Initial centroids: rows init_idx (host int64[k], distinct, in
+ * [0, n)) or, when prev_assign (host or device per assign_where, int32[n]) is
+ * given, the means of that assignment with an empty cluster taking row
+ * init_idx[j].  Assignment by squared Euclidean distance, ties to the lowest
+ * index, decided exactly in float64 whenever the float32 margin is within its
+ * error bound; update by means (exact fixed-point sums), an empty cluster keeps
+ * its centroid; stop when the assignment repeats or after max_iter passes
+ * (<= 0: the context's max_iter).  Outputs: assign_out int32[n] (host or
+ * device per assign_where), centroids_out host double[k*d] or NULL,
+ * inertia_out = sum_i ||y_i - c_{a(i)}||^2, iters_out = assignment passes. */
+csc_status csc_kmeans(csc_ctx* ctx, const void* Y, int y_dtype, int64_t n, int d, int64_t ldy,
+                      int y_where, int k, const int64_t* init_idx, const int32_t* prev_assign,
+                      int max_iter, int32_t* assign_out, int assign_where, double* centroids_out,
+                      double* inertia_out, int* iters_out);
+
+/* ---------------------------------------------------------------- Algorithm 1 */
+
+/* Algorithm 1 step 1 (Section 3.3): cutoff lambda_c whose eigencount of the d
+ * signals the next csc_filter will draw (seed, the next d global column ids) is
+ * within tau of k, by one moment pass of order m and the dichotomy on [0, 2].
+ * Stores the cutoff on the context.  Outputs may be NULL. */
+csc_status csc_estimate_lambda_k(csc_ctx* ctx, int k, int m, int d, uint64_t seed,
+                                 double* lambda_out, double* count_out, int* evals_out);
+
+/* Algorithm 1 steps 4-7 and Eq. 6 on the current snapshot.  First snapshot (or
+ * p == 0): filter d new signals.  Later snapshots: keep dp = floor(p d) columns of
+ * Theta_{t-1} (the ring slots filtered most recently) and filter dq = d - dp new
+ * signals.  Cutoff: lambda_c >= 0 is used as given; lambda_c < 0 uses the
+ * context's current cutoff (estimated first when there is none; needs k > 0).
+ * With k > 0 the eigencount of the new block is checked and the cutoff refined
+ * by the dichotomy when |count - k| > tau, after which the block is refiltered
+ * (same signals).  The new columns overwrite the oldest ring slots; the
+ * row-normalised Theta_t is prepared for csc_cluster.  d must stay the same
+ * across snapshots.  Outputs (may be NULL): final cutoff, its eigencount,
+ * dichotomy evaluations (0 when lambda_c was given or k <= 0), columns filtered. */
+csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k, double lambda_c,
+                      double* lambda_out, double* count_out, int* evals_out, int* cols_out);
+
+/* Copies Theta_t (normalized = 0, float32 ring in slot order) or the row-normalised
+ * features y_i = theta_i / ||theta_i|| (normalized = 1) into dst (n x d, dtype
+ * CSC_F32 or CSC_BF16, leading dimension ld >= d, host or device per where). */
+csc_status csc_get_features(csc_ctx* ctx, void* dst, int dtype, int64_t ld, int normalized,
+                            int where);
+
+/* Trace moments mu_0..mu_{2m} of the last filtering pass (host double[len], len <= 2m+1). */
+csc_status csc_get_moments(csc_ctx* ctx, double* mu_out, int len);
+
+/* Algorithm 1 steps 2 and 8: k-means on the row-normalised Theta_t.  The first
+ * call on a context starts from Forgy rows init_idx (host int64[k]; NULL = draw
+ * with the counter-based generator, key seed ^ (t * 0x9E3779B97F4A7C15)); later
+ * calls warm-start from the previous assignment (an empty cluster takes row
+ * init_idx[j]).  assign_out int32[n] host or device per where; cost_out =
+ * C_Theta = sqrt(inertia) (Eq. 1 with Theta's row-normalised features);
+ * iters_out = Lloyd assignment passes.  Outputs may be NULL except assign_out. */
+csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_idx,
+                       int32_t* assign_out, int where, double* cost_out, int* iters_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSC_H */

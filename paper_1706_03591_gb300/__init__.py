@@ -1,0 +1,277 @@
+"""GB300-native dynamic compressive spectral clustering (arXiv:1706.03591).
+
+Thin Python binding of libcsc's C ABI (include/csc.h): every function below
+has the name of the C entry point it calls and only marshals arguments.
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); every step of the method runs in the CUDA library.  Importing this
+package does not need a GPU; calling into the library does.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import CSC_BF16, CSC_DEVICE, CSC_F32, CSC_HOST  # noqa: F401
+
+__all__ = [
+    "CscError", "Context", "csc_create", "csc_destroy", "csc_last_error", "csc_set_graph",
+    "csc_filter_coeffs", "csc_count_tolerance", "csc_count_from_moments",
+    "csc_lambda_search_moments", "csc_signals", "csc_cheb_filter", "csc_kmeans",
+    "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
+    "csc_abi_version", "csc_get_stats",
+]
+
+
+class CscError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"csc status {status}: {message}")
+        self.status = status
+
+
+def _lib():
+    return _abi.load()
+
+
+def _check(status: int, handle=None, what: str = ""):
+    if status != _abi.CSC_OK:
+        lib = _lib()
+        msg = lib.csc_last_error(handle).decode() if handle else ""
+        if not msg:
+            msg = lib.csc_status_string(status).decode()
+        raise CscError(status, f"{what}: {msg}" if what else msg)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _arr(x, kind: str):
+    """(pointer, where, dtype-code, leading dimension) of a 1-D/2-D array argument."""
+    if x is None:
+        return None, _abi.CSC_HOST, _abi.CSC_F32, 0
+    if _is_torch(x):
+        import torch
+        if x.dim() == 2 and x.stride(1) != 1 or x.dim() == 1 and x.stride(0) != 1:
+            raise ValueError(f"{kind}: innermost dimension must be contiguous")
+        where = _abi.CSC_DEVICE if x.is_cuda else _abi.CSC_HOST
+        code = _abi.CSC_BF16 if x.dtype == torch.bfloat16 else _abi.CSC_F32
+        ld = x.stride(0) if x.dim() == 2 else 0
+        return C.c_void_p(x.data_ptr()), where, code, ld
+    a = np.asarray(x)
+    if a.ndim == 2 and a.strides[1] != a.itemsize or a.ndim == 1 and a.strides[0] != a.itemsize:
+        raise ValueError(f"{kind}: innermost dimension must be contiguous")
+    ld = a.strides[0] // a.itemsize if a.ndim == 2 else 0
+    return C.c_void_p(a.ctypes.data), _abi.CSC_HOST, _abi.CSC_F32, ld
+
+
+def csc_abi_version() -> int:
+    return _lib().csc_abi_version()
+
+
+def csc_create(opts: dict | None = None, stream=None):
+    """Creates a context; `stream` is a cudaStream_t integer (default: torch's current stream)."""
+    lib = _lib()
+    o = _abi.csc_opts()
+    lib.csc_default_opts(C.byref(o))
+    for key, val in (opts or {}).items():
+        setattr(o, key, val)
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            stream = None
+    h = C.c_void_p()
+    _check(lib.csc_create(C.byref(h), C.byref(o), C.c_void_p(stream or 0)), None, "csc_create")
+    return h
+
+
+def csc_destroy(h) -> None:
+    _lib().csc_destroy(h)
+
+
+def csc_last_error(h) -> str:
+    return _lib().csc_last_error(h).decode()
+
+
+def csc_get_stats(h, reset: bool = False) -> dict:
+    st = _abi.csc_stats()
+    _check(_lib().csc_get_stats(h, C.byref(st), int(reset)), h, "csc_get_stats")
+    return dict(launches=st.launches, step_launches=st.step_launches, step_ms=st.step_ms,
+                filter_passes=st.filter_passes, tile=st.tile)
+
+
+def csc_set_graph(h, n: int, row_ptr, col_idx, vals=None) -> None:
+    rp, where, _, _ = _arr(row_ptr, "row_ptr")
+    ci, where2, _, _ = _arr(col_idx, "col_idx")
+    vv, where3, _, _ = _arr(vals, "vals")
+    if where2 != where or (vals is not None and where3 != where):
+        raise ValueError("row_ptr, col_idx and vals must live in the same memory")
+    nnz = int(col_idx.numel() if _is_torch(col_idx) else np.asarray(col_idx).size)
+    _check(_lib().csc_set_graph(h, n, nnz, rp, ci, vv, where), h, "csc_set_graph")
+
+
+def csc_filter_coeffs(m: int, lambda_c: float) -> np.ndarray:
+    a = np.zeros(m + 1)
+    _check(_lib().csc_filter_coeffs(m, lambda_c, a.ctypes.data_as(C.POINTER(C.c_double))))
+    return a
+
+
+def csc_count_tolerance(k: int, c: int) -> float:
+    return _lib().csc_count_tolerance(k, c)
+
+
+def csc_count_from_moments(m: int, mu, lambda_c: float, d: int, c: int) -> float:
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    out = C.c_double()
+    _check(_lib().csc_count_from_moments(m, mu.ctypes.data_as(C.POINTER(C.c_double)), lambda_c, d, c,
+                                         C.byref(out)))
+    return out.value
+
+
+def csc_lambda_search_moments(m, mu, d, c, k, tau, lambda_prev=-1.0, max_steps=30):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    lam, cnt, ev = C.c_double(), C.c_double(), C.c_int()
+    _check(_lib().csc_lambda_search_moments(m, mu.ctypes.data_as(C.POINTER(C.c_double)), d, c, k, tau,
+                                            lambda_prev, max_steps, C.byref(lam), C.byref(cnt),
+                                            C.byref(ev)))
+    return lam.value, cnt.value, ev.value
+
+
+def csc_signals(h, seed: int, n: int, col0: int, c: int, d: int, out) -> None:
+    ptr, where, code, ld = _arr(out, "out")
+    _check(_lib().csc_signals(h, seed, n, col0, c, d, ptr, code, ld or c, where), h, "csc_signals")
+
+
+def csc_cheb_filter(h, m: int, lambda_c: float, R, psi_out=None, want_moments: bool = True):
+    """Filters the caller's block R into psi_out; returns the 2m+1 trace moments (or None)."""
+    rp, rw, rcode, ldr = _arr(R, "R")
+    c = int(R.shape[1])
+    pp, pw, _, ldp = _arr(psi_out, "psi_out")
+    mu = np.zeros(2 * m + 1) if want_moments else None
+    _check(_lib().csc_cheb_filter(h, m, lambda_c, rp, rcode, c, ldr or c, rw, pp, ldp or c, pw,
+                                  mu.ctypes.data_as(C.POINTER(C.c_double)) if mu is not None else None),
+           h, "csc_cheb_filter")
+    return mu
+
+
+def csc_kmeans(h, Y, k: int, init_idx, prev_assign=None, max_iter: int = 0, assign_out=None,
+               want_centroids: bool = True):
+    """Lloyd k-means of the rows of Y; returns dict(assign, centroids, inertia, iters)."""
+    yp, yw, ycode, ldy = _arr(Y, "Y")
+    n, d = int(Y.shape[0]), int(Y.shape[1])
+    idx = np.ascontiguousarray(init_idx, dtype=np.int64)
+    if assign_out is None:
+        assign_out = np.zeros(n, dtype=np.int32)
+    ap, aw, _, _ = _arr(assign_out, "assign_out")
+    pv = None
+    if prev_assign is not None:
+        pv, pw, _, _ = _arr(prev_assign, "prev_assign")
+        if pw != aw:
+            raise ValueError("prev_assign must live where assign_out lives")
+    cents = np.zeros((k, d)) if want_centroids else None
+    inertia, iters = C.c_double(), C.c_int()
+    _check(_lib().csc_kmeans(h, yp, ycode, n, d, ldy or d, yw, k, C.c_void_p(idx.ctypes.data), pv,
+                             max_iter, ap, aw,
+                             cents.ctypes.data_as(C.POINTER(C.c_double)) if cents is not None else None,
+                             C.byref(inertia), C.byref(iters)), h, "csc_kmeans")
+    return dict(assign=assign_out, centroids=cents, inertia=inertia.value, iters=iters.value)
+
+
+def csc_estimate_lambda_k(h, k: int, m: int, d: int, seed: int):
+    lam, cnt, ev = C.c_double(), C.c_double(), C.c_int()
+    _check(_lib().csc_estimate_lambda_k(h, k, m, d, seed, C.byref(lam), C.byref(cnt), C.byref(ev)), h,
+           "csc_estimate_lambda_k")
+    return lam.value, cnt.value, ev.value
+
+
+def csc_filter(h, m: int, d: int, p: float, seed: int, k: int = 0, lambda_c: float = -1.0):
+    """Algorithm 1 steps 4-7; returns (lambda_c, count, dichotomy evaluations, columns filtered)."""
+    lam, cnt, ev, cols = C.c_double(), C.c_double(), C.c_int(), C.c_int()
+    _check(_lib().csc_filter(h, m, d, p, seed, k, lambda_c, C.byref(lam), C.byref(cnt), C.byref(ev),
+                             C.byref(cols)), h, "csc_filter")
+    return lam.value, cnt.value, ev.value, cols.value
+
+
+def csc_get_features(h, dst, normalized: bool = False) -> None:
+    ptr, where, code, ld = _arr(dst, "dst")
+    _check(_lib().csc_get_features(h, ptr, code, ld or int(dst.shape[1]), int(normalized), where), h,
+           "csc_get_features")
+
+
+def csc_get_moments(h, length: int) -> np.ndarray:
+    mu = np.zeros(length)
+    _check(_lib().csc_get_moments(h, mu.ctypes.data_as(C.POINTER(C.c_double)), length), h,
+           "csc_get_moments")
+    return mu
+
+
+def csc_cluster(h, k: int, seed: int, init_idx, assign_out):
+    """Algorithm 1 step 8; writes assign_out and returns (cost C_Theta, Lloyd passes)."""
+    idx = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int64)
+    ap, aw, _, _ = _arr(assign_out, "assign_out")
+    cost, iters = C.c_double(), C.c_int()
+    _check(_lib().csc_cluster(h, k, seed, None if idx is None else C.c_void_p(idx.ctypes.data), ap, aw,
+                              C.byref(cost), C.byref(iters)), h, "csc_cluster")
+    return cost.value, iters.value
+
+
+class Context:
+    """Owns a csc context handle; methods forward to the csc_* functions above."""
+
+    def __init__(self, opts: dict | None = None, stream=None):
+        self.h = csc_create(opts, stream)
+
+    def close(self):
+        if self.h:
+            csc_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self, reset=False):
+        return csc_get_stats(self.h, reset)
+
+    def set_graph(self, n, row_ptr, col_idx, vals=None):
+        csc_set_graph(self.h, n, row_ptr, col_idx, vals)
+
+    def signals(self, seed, n, col0, c, d, out):
+        csc_signals(self.h, seed, n, col0, c, d, out)
+
+    def cheb_filter(self, m, lambda_c, R, psi_out=None, want_moments=True):
+        return csc_cheb_filter(self.h, m, lambda_c, R, psi_out, want_moments)
+
+    def kmeans(self, Y, k, init_idx, prev_assign=None, max_iter=0, assign_out=None, want_centroids=True):
+        return csc_kmeans(self.h, Y, k, init_idx, prev_assign, max_iter, assign_out, want_centroids)
+
+    def estimate_lambda_k(self, k, m, d, seed):
+        return csc_estimate_lambda_k(self.h, k, m, d, seed)
+
+    def filter(self, m, d, p, seed, k=0, lambda_c=-1.0):
+        return csc_filter(self.h, m, d, p, seed, k, lambda_c)
+
+    def get_features(self, dst, normalized=False):
+        csc_get_features(self.h, dst, normalized)
+
+    def get_moments(self, length):
+        return csc_get_moments(self.h, length)
+
+    def cluster(self, k, seed, init_idx, assign_out):
+        return csc_cluster(self.h, k, seed, init_idx, assign_out)
+
+    @property
+    def last_error(self):
+        return csc_last_error(self.h)

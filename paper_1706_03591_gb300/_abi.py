@@ -1,0 +1,89 @@
+"""ctypes declarations of libcsc's C ABI (include/csc.h).
+
+Loading fails loudly when the shared library is missing: there is no CPU
+fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcsc.so")
+
+CSC_OK, CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA, CSC_ETIMEOUT, CSC_ESTATE = range(6)
+CSC_HOST, CSC_DEVICE = 0, 1
+CSC_F32, CSC_BF16 = 0, 1
+
+
+class csc_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("count_tol", C.c_double),
+        ("max_bisect", C.c_int),
+        ("max_iter", C.c_int),
+        ("col_tile", C.c_int),
+        ("checked", C.c_int),
+        ("timing", C.c_int),
+    ]
+
+
+class csc_stats(C.Structure):
+    _fields_ = [
+        ("launches", C.c_int64),
+        ("step_launches", C.c_int64),
+        ("step_ms", C.c_double),
+        ("filter_passes", C.c_int64),
+        ("tile", C.c_int64),
+    ]
+
+
+_p = C.c_void_p
+_i32, _i64, _u64, _dbl = C.c_int, C.c_int64, C.c_uint64, C.c_double
+_pd, _pi = C.POINTER(C.c_double), C.POINTER(C.c_int)
+
+# name -> (restype, argtypes); the order matches include/csc.h
+SIGNATURES = {
+    "csc_default_opts": (None, [C.POINTER(csc_opts)]),
+    "csc_status_string": (C.c_char_p, [_i32]),
+    "csc_abi_version": (_i32, []),
+    "csc_create": (_i32, [C.POINTER(_p), C.POINTER(csc_opts), _p]),
+    "csc_destroy": (None, [_p]),
+    "csc_last_error": (C.c_char_p, [_p]),
+    "csc_get_stats": (_i32, [_p, C.POINTER(csc_stats), _i32]),
+    "csc_set_graph": (_i32, [_p, _i64, _i64, _p, _p, _p, _i32]),
+    "csc_filter_coeffs": (_i32, [_i32, _dbl, _pd]),
+    "csc_count_tolerance": (_dbl, [_i32, _i32]),
+    "csc_count_from_moments": (_i32, [_i32, _pd, _dbl, _i32, _i32, _pd]),
+    "csc_lambda_search_moments": (_i32, [_i32, _pd, _i32, _i32, _i32, _dbl, _dbl, _i32, _pd, _pd, _pi]),
+    "csc_signals": (_i32, [_p, _u64, _i64, _i64, _i32, _i32, _p, _i32, _i64, _i32]),
+    "csc_cheb_filter": (_i32, [_p, _i32, _dbl, _p, _i32, _i32, _i64, _i32, _p, _i64, _i32, _pd]),
+    "csc_kmeans": (_i32, [_p, _p, _i32, _i64, _i32, _i64, _i32, _i32, _p, _p, _i32, _p, _i32, _pd,
+                          _pd, _pi]),
+    "csc_estimate_lambda_k": (_i32, [_p, _i32, _i32, _i32, _u64, _pd, _pd, _pi]),
+    "csc_filter": (_i32, [_p, _i32, _i32, _dbl, _u64, _i32, _dbl, _pd, _pd, _pi, _pi]),
+    "csc_get_features": (_i32, [_p, _p, _i32, _i64, _i32, _i32]),
+    "csc_get_moments": (_i32, [_p, _pd, _i32]),
+    "csc_cluster": (_i32, [_p, _i32, _u64, _p, _p, _i32, _pd, _pi]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """The loaded library with argtypes set (cached)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"libcsc.so not found at {path}: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib

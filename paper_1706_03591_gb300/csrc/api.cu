@@ -1,0 +1,833 @@
+// C ABI of libcsc (declarations and contracts in include/csc.h).
+//
+// Host-side logic of the method lives here: the Jackson-damped coefficients
+// (Section 3.3), the eigencount from trace moments, the dichotomy for the cutoff
+// (Algorithm 1 steps 1 and 7, Section 4.1), the feature ring of Eq. 6 and the
+// Lloyd driver.  Every device step runs in the kernels of the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "csc_internal.h"
+
+using csc::DevBuf;
+
+struct csc_ctx {
+  csc_opts opts;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  csc::Graph g;
+  // filtering
+  DevBuf tbuf[3];
+  DevBuf psi;
+  DevBuf part;
+  DevBuf ef;          // reduced E/F sums, double[2m+1]
+  DevBuf coef;        // float[m+1]
+  DevBuf rstage;      // caller signal block staged on the device
+  std::vector<double> mu;
+  int last_m = 0;
+  // feature ring (Eq. 6)
+  int64_t ring_n = 0;
+  int ring_d = 0;
+  DevBuf theta;       // float n x d
+  DevBuf y;           // n x d, float or bf16 (row-normalised features)
+  DevBuf slot_src;    // int[d]
+  std::vector<int64_t> stamp;
+  int64_t t = 0;
+  int64_t next_id = 0;
+  bool has_lambda = false;
+  double lambda = 0.0;
+  // k-means
+  csc::KmeansState km;
+  DevBuf prev_assign;
+  int prev_k = 0;
+  bool has_prev = false;
+  DevBuf ystage;      // caller features staged on the device
+  DevBuf astage;      // caller assignment staged on the device
+  DevBuf out_stage;   // conversions before a host copy
+  DevBuf bad;         // CSR violation counter
+  // counters (csc_get_stats)
+  int64_t launches = 0, step_launches = 0, filter_passes = 0;
+  double step_ms = 0.0;
+  int last_tile = 0;
+  std::vector<cudaEvent_t> events;  // timing event pairs, one per column tile
+};
+
+namespace csc {
+
+bool ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return true;
+  release(b);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  b.ptr = p;
+  b.bytes = bytes;
+  return true;
+}
+
+void release(DevBuf& b) {
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+int grid_for(const void* kernel, int block, size_t smem) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+  return std::max(1, per_sm) * num_sms();
+}
+
+}  // namespace csc
+
+namespace {
+
+// ------------------------------------------------------------------ host math (Section 3.3)
+
+void coeffs(int m, double lambda_c, double* a) {
+  const double x_c = std::min(1.0, std::max(-1.0, lambda_c - 1.0));
+  const double theta = std::acos(x_c);
+  const double mp2 = m + 2.0;
+  const double alpha = M_PI / mp2;
+  for (int j = 0; j <= m; ++j) {
+    const double c = j == 0 ? (M_PI - theta) / M_PI : -2.0 * std::sin(j * theta) / (j * M_PI);
+    const double g = ((mp2 - j) * std::sin(alpha) * std::cos(j * alpha) +
+                      std::cos(alpha) * std::sin(j * alpha)) / (mp2 * std::sin(alpha));
+    a[j] = g * c;
+  }
+}
+
+double count_moments(int m, const double* mu, const double* a, int d, int c) {
+  double s = 0.0;
+  for (int i = 0; i <= m; ++i)
+    for (int j = 0; j <= m; ++j) s += a[i] * a[j] * 0.5 * (mu[i + j] + mu[std::abs(i - j)]);
+  return (double)d / (double)c * s;
+}
+
+double tolerance(int k, int c) { return std::max(0.5, 2.0 * std::sqrt(2.0 * k / (double)c)); }
+
+// Dichotomy with the control flow of Algorithm 1 step 7 (see csc.h).
+template <typename F>
+void search(F count, int k, double tau, double lam_prev, int max_steps, double* lam_out,
+            double* cnt_out, int* evals_out) {
+  int evals = 0;
+  double lam = 0.0, cnt = 0.0, lo = 0.0, hi = 2.0;
+  auto ev = [&](double x) { ++evals; return count(x); };
+  auto done = [&]() { *lam_out = lam; *cnt_out = cnt; *evals_out = evals; };
+  if (lam_prev >= 0.0) {
+    lam = lam_prev;
+    cnt = ev(lam_prev);
+    if (std::fabs(cnt - k) <= tau) return done();
+    const double dir = cnt < k ? 1.0 : -1.0;
+    double step = 0.01, prev = lam_prev;
+    bool bracketed = false;
+    while (evals < max_steps) {
+      const double probe = std::min(2.0, std::max(0.0, lam_prev + dir * step));
+      lam = probe;
+      cnt = ev(probe);
+      if (std::fabs(cnt - k) <= tau) return done();
+      const bool crossed = dir > 0 ? (cnt > k) : (cnt < k);
+      if (crossed || probe == 0.0 || probe == 2.0) {
+        lo = std::min(prev, probe);
+        hi = std::max(prev, probe);
+        bracketed = true;
+        break;
+      }
+      prev = probe;
+      step *= 2.0;
+    }
+    if (!bracketed) return done();
+  }
+  while (evals < max_steps) {
+    const double mid = 0.5 * (lo + hi);
+    lam = mid;
+    cnt = ev(mid);
+    if (std::fabs(cnt - k) <= tau) return done();
+    if (cnt < k) lo = mid; else hi = mid;
+  }
+  done();
+}
+
+// Philox-4x32-10 on the host (Forgy draws when the caller passes no indices).
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1, n3 = (uint32_t)p0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+  }
+}
+
+std::vector<int64_t> forgy_draw(uint64_t seed, int64_t n, int k) {
+  std::vector<int64_t> out;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int j = 0; j < k; ++j) {
+    for (uint32_t attempt = 0;; ++attempt) {
+      uint32_t c[4] = {(uint32_t)j, attempt, 0u, 1u};
+      philox_host(c, k0, k1);
+      const unsigned __int128 u = ((unsigned __int128)(((uint64_t)c[0] << 32) | c[1])) * (uint64_t)n;
+      const int64_t idx = (int64_t)(u >> 64);
+      if (std::find(out.begin(), out.end(), idx) == out.end()) {
+        out.push_back(idx);
+        break;
+      }
+    }
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------ context helpers
+
+csc_status fail(csc_ctx* ctx, csc_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+#define CUDA_OK(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, CSC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+  } while (0)
+
+#define ALLOC_OK(expr) \
+  do {                 \
+    if (!(expr)) return fail(ctx, CSC_ENOMEM, "device allocation failed: " #expr); \
+  } while (0)
+
+int tile_width(const csc_ctx* ctx, int64_t n, int c) {
+  if (ctx->opts.col_tile > 0) return ctx->opts.col_tile;
+  // Large graphs: narrow tiles keep the gathered block of one tile near L2 size.
+  const double block_bytes = (double)n * 4.0;
+  int w = 8;
+  while (w < 128 && w < c) w *= 2;
+  while (w > 8 && block_bytes * w * 3.0 > 96.0e6) w /= 2;
+  return w;
+}
+
+bool valid_tile(int w) { return w == 8 || w == 16 || w == 32 || w == 64 || w == 128; }
+
+// Signal source of a filtering pass: Philox columns or a caller block already on the device.
+struct Source {
+  bool philox = true;
+  uint64_t seed = 0;
+  int64_t col0 = 0;
+  int d = 1;
+  int dtype = CSC_F32;
+  const void* R = nullptr;
+  int64_t ldr = 0;
+};
+
+// Chebyshev recursion over c columns in tiles.  psi_dst: device float, leading dim ldp
+// (nullptr: moments only).  Fills ctx->mu (2m+1 trace moments).
+csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source& src, float* psi_dst,
+                      int64_t ldp) {
+  const int64_t n = ctx->g.n;
+  cudaStream_t s = ctx->stream;
+  const int w = tile_width(ctx, n, c);
+  if (!valid_tile(w)) return fail(ctx, CSC_EINVAL, "col_tile must be 8, 16, 32, 64 or 128");
+  const int ntiles = (c + w - 1) / w;
+  const int grid = csc::cheb_grid(w);
+  ctx->last_tile = w;
+  const int rows = 2 * m + 1;
+  for (auto& b : ctx->tbuf) ALLOC_OK(csc::ensure(b, (size_t)std::max<int64_t>(n, 1) * w * 4));
+  ALLOC_OK(csc::ensure(ctx->part, (size_t)ntiles * rows * grid * 8));
+  ALLOC_OK(csc::ensure(ctx->ef, (size_t)rows * 8));
+  ALLOC_OK(csc::ensure(ctx->coef, (size_t)(m + 1) * 4));
+  std::vector<double> a(m + 1);
+  coeffs(m, lambda_c, a.data());
+  std::vector<float> af(a.begin(), a.end());
+  CUDA_OK(cudaMemcpyAsync(ctx->coef.ptr, af.data(), af.size() * 4, cudaMemcpyHostToDevice, s));
+  const int t0_dtype = src.philox ? ctx->opts.precision : src.dtype;
+  const bool timed = ctx->opts.timing && m >= 2;
+  if (timed) {
+    while ((int)ctx->events.size() < 2 * ntiles) {
+      cudaEvent_t e;
+      CUDA_OK(cudaEventCreate(&e));
+      ctx->events.push_back(e);
+    }
+  }
+  const float inv_sqrt_d = (float)(1.0 / std::sqrt((double)src.d));
+  double* part = csc::as<double>(ctx->part);
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int c0 = tile * w;
+    const int valid = std::min(w, c - c0);
+    if (src.philox)
+      CUDA_OK(csc::launch_signals(ctx->tbuf[0].ptr, t0_dtype, n, w, w, src.seed, src.col0 + c0, valid,
+                                  inv_sqrt_d, s));
+    else
+      CUDA_OK(csc::launch_copy_tile(ctx->tbuf[0].ptr, src.R, t0_dtype, n, w, src.ldr, c0, valid, s));
+    double* tile_part = part + (size_t)tile * rows * grid;
+    csc::StepArgs sa{};
+    sa.n = n;
+    sa.row_ptr = csc::as<int64_t>(ctx->g.row_ptr);
+    sa.col = csc::as<int32_t>(ctx->g.col);
+    sa.val = ctx->g.weighted ? csc::as<float>(ctx->g.val) : nullptr;
+    sa.scale = csc::as<float>(ctx->g.scale);
+    sa.psi = psi_dst ? psi_dst + c0 : nullptr;
+    sa.ldp = ldp;
+    sa.coef = csc::as<float>(ctx->coef);
+    sa.w = w;
+    sa.tg = ctx->tbuf[0].ptr;
+    sa.tp = nullptr;
+    sa.tn = csc::as<float>(ctx->tbuf[1]);
+    sa.j = 0;
+    sa.part = tile_part;
+    CUDA_OK(csc::launch_cheb_first(sa, t0_dtype, grid, s));
+    if (timed) CUDA_OK(cudaEventRecord(ctx->events[2 * tile], s));
+    for (int j = 1; j < m; ++j) {
+      sa.tg = ctx->tbuf[j % 3].ptr;
+      sa.tp = ctx->tbuf[(j - 1) % 3].ptr;
+      sa.tn = csc::as<float>(ctx->tbuf[(j + 1) % 3]);
+      sa.j = j;
+      sa.part = tile_part + (size_t)(2 * (j + 1) - 1) * grid;
+      CUDA_OK(csc::launch_cheb_step(sa, j == 1 ? t0_dtype : CSC_F32, grid, s));
+    }
+    if (timed) CUDA_OK(cudaEventRecord(ctx->events[2 * tile + 1], s));
+    ctx->launches += m + 1;
+    ctx->filter_passes += 1;
+  }
+  ctx->launches += 1;
+  CUDA_OK(csc::launch_reduce_partials(part, rows, grid, ntiles, (int64_t)rows * grid,
+                                      csc::as<double>(ctx->ef), s));
+  std::vector<double> ef(rows);
+  CUDA_OK(cudaMemcpyAsync(ef.data(), ctx->ef.ptr, rows * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (timed) {
+    for (int tile = 0; tile < ntiles; ++tile) {
+      float ms = 0.f;
+      CUDA_OK(cudaEventElapsedTime(&ms, ctx->events[2 * tile], ctx->events[2 * tile + 1]));
+      ctx->step_ms += ms;
+      ctx->step_launches += m - 1;
+    }
+  }
+  ctx->mu.assign(2 * m + 1, 0.0);
+  ctx->mu[0] = ef[0];
+  if (m >= 1) {
+    ctx->mu[1] = ef[2];
+    for (int q = 1; q <= m; ++q) {
+      ctx->mu[2 * q] = 2.0 * ef[2 * q - 1] - ctx->mu[0];
+      if (q >= 2) ctx->mu[2 * q - 1] = 2.0 * ef[2 * q] - ctx->mu[1];
+    }
+  }
+  ctx->last_m = m;
+  return CSC_OK;
+}
+
+double count_at(const csc_ctx* ctx, double lam, int d, int c) {
+  std::vector<double> a(ctx->last_m + 1);
+  coeffs(ctx->last_m, lam, a.data());
+  return count_moments(ctx->last_m, ctx->mu.data(), a.data(), d, c);
+}
+
+size_t dtype_size(int dtype) { return dtype == CSC_BF16 ? 2 : 4; }
+bool valid_dtype(int dtype) { return dtype == CSC_F32 || dtype == CSC_BF16; }
+bool valid_where(int where) { return where == CSC_HOST || where == CSC_DEVICE; }
+
+csc_status validate_host_csr(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rp,
+                             const int32_t* ci, const float* vals) {
+  if (rp[0] != 0 || rp[n] != nnz) return fail(ctx, CSC_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] = nnz");
+  for (int64_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) return fail(ctx, CSC_EINVAL, "row_ptr must be non-decreasing");
+    int64_t prev = -1;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int64_t c = ci[p];
+      if (c < 0 || c >= n) return fail(ctx, CSC_EINVAL, "col_idx out of range");
+      if (c == i) return fail(ctx, CSC_EINVAL, "self-loops are not allowed (simple graph)");
+      if (c <= prev) return fail(ctx, CSC_EINVAL, "columns of a row must be strictly increasing");
+      if (vals && !(vals[p] > 0.0f)) return fail(ctx, CSC_EINVAL, "edge weights must be positive");
+      prev = c;
+    }
+  }
+  return CSC_OK;
+}
+
+// Copies an n x d device block (dtype src_dtype, ld_src) to a caller destination.
+csc_status copy_out(csc_ctx* ctx, const void* src, int src_dtype, int64_t ld_src, int64_t n, int d,
+                    void* dst, int dst_dtype, int64_t ld_dst, int where) {
+  cudaStream_t s = ctx->stream;
+  const size_t esz = dtype_size(dst_dtype);
+  ctx->launches += 1;
+  if (where == CSC_DEVICE) {
+    CUDA_OK(csc::launch_convert(src, src_dtype, ld_src, dst, dst_dtype, ld_dst, n, d, s));
+    return CSC_OK;
+  }
+  ALLOC_OK(csc::ensure(ctx->out_stage, (size_t)std::max<int64_t>(n, 1) * d * esz));
+  CUDA_OK(csc::launch_convert(src, src_dtype, ld_src, ctx->out_stage.ptr, dst_dtype, d, n, d, s));
+  if (n > 0 && d > 0)
+    CUDA_OK(cudaMemcpy2DAsync(dst, ld_dst * esz, ctx->out_stage.ptr, d * esz, d * esz, n,
+                              cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  return CSC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void csc_default_opts(csc_opts* o) {
+  if (!o) return;
+  o->precision = CSC_F32;
+  o->count_tol = 0.0;
+  o->max_bisect = 30;
+  o->max_iter = 100;
+  o->col_tile = 0;
+  o->checked = 0;
+  o->timing = 0;
+}
+
+const char* csc_status_string(csc_status s) {
+  switch (s) {
+    case CSC_OK: return "ok";
+    case CSC_EINVAL: return "invalid argument";
+    case CSC_ENOMEM: return "out of memory";
+    case CSC_ECUDA: return "CUDA error";
+    case CSC_ETIMEOUT: return "device wait timed out";
+    case CSC_ESTATE: return "invalid call order";
+  }
+  return "unknown status";
+}
+
+int csc_abi_version(void) { return CSC_ABI_VERSION; }
+
+csc_status csc_create(csc_ctx** out, const csc_opts* opts, void* cuda_stream) {
+  if (!out) return CSC_EINVAL;
+  *out = nullptr;
+  csc_opts o;
+  csc_default_opts(&o);
+  if (opts) o = *opts;
+  if (!valid_dtype(o.precision) || o.max_bisect < 1 || o.max_iter < 1 ||
+      (o.col_tile != 0 && !valid_tile(o.col_tile)))
+    return CSC_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return CSC_ECUDA;
+  }
+  csc_ctx* ctx = new (std::nothrow) csc_ctx();
+  if (!ctx) return CSC_ENOMEM;
+  ctx->opts = o;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->device = dev;
+  *out = ctx;
+  return CSC_OK;
+}
+
+void csc_destroy(csc_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  DevBuf* bufs[] = {&ctx->g.row_ptr, &ctx->g.col, &ctx->g.val, &ctx->g.scale, &ctx->g.deg,
+                    &ctx->tbuf[0], &ctx->tbuf[1], &ctx->tbuf[2], &ctx->psi, &ctx->part, &ctx->ef,
+                    &ctx->coef, &ctx->rstage, &ctx->theta, &ctx->y, &ctx->slot_src,
+                    &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad};
+  for (DevBuf* b : bufs) csc::release(*b);
+  csc::kmeans_release(ctx->km);
+  delete ctx;
+}
+
+const char* csc_last_error(const csc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+csc_status csc_get_stats(csc_ctx* ctx, csc_stats* out, int reset) {
+  if (!ctx || !out) return CSC_EINVAL;
+  out->launches = ctx->launches;
+  out->step_launches = ctx->step_launches;
+  out->step_ms = ctx->step_ms;
+  out->filter_passes = ctx->filter_passes;
+  out->tile = ctx->last_tile;
+  if (reset) {
+    ctx->launches = ctx->step_launches = ctx->filter_passes = 0;
+    ctx->step_ms = 0.0;
+  }
+  return CSC_OK;
+}
+
+csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                         const int32_t* col_idx, const float* vals, int where) {
+  if (!ctx) return CSC_EINVAL;
+  if (n < 1 || nnz < 0 || n > INT32_MAX || !row_ptr || (nnz > 0 && !col_idx) || !valid_where(where))
+    return fail(ctx, CSC_EINVAL, "csc_set_graph: bad sizes or pointers");
+  if (ctx->t > 0 && n != ctx->ring_n)
+    return fail(ctx, CSC_EINVAL, "csc_set_graph: the vertex set is fixed across snapshots");
+  if (where == CSC_HOST) {
+    csc_status st = validate_host_csr(ctx, n, nnz, row_ptr, col_idx, vals);
+    if (st != CSC_OK) return st;
+  }
+  cudaStream_t s = ctx->stream;
+  csc::Graph& g = ctx->g;
+  ALLOC_OK(csc::ensure(g.row_ptr, (size_t)(n + 1) * 8));
+  ALLOC_OK(csc::ensure(g.col, (size_t)nnz * 4));
+  ALLOC_OK(csc::ensure(g.scale, (size_t)n * 4));
+  ALLOC_OK(csc::ensure(g.deg, (size_t)n * 8));
+  const cudaMemcpyKind kind = where == CSC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CUDA_OK(cudaMemcpyAsync(g.row_ptr.ptr, row_ptr, (size_t)(n + 1) * 8, kind, s));
+  if (nnz > 0) CUDA_OK(cudaMemcpyAsync(g.col.ptr, col_idx, (size_t)nnz * 4, kind, s));
+  g.weighted = vals != nullptr;
+  if (g.weighted) {
+    ALLOC_OK(csc::ensure(g.val, (size_t)nnz * 4));
+    if (nnz > 0) CUDA_OK(cudaMemcpyAsync(g.val.ptr, vals, (size_t)nnz * 4, kind, s));
+  }
+  g.n = n;
+  g.nnz = nnz;
+  if (where == CSC_DEVICE && ctx->opts.checked) {
+    ALLOC_OK(csc::ensure(ctx->bad, 16));
+    CUDA_OK(cudaMemsetAsync(ctx->bad.ptr, 0, 8, s));
+    CUDA_OK(csc::launch_graph_check(g, csc::as<unsigned long long>(ctx->bad), s));
+    ctx->launches += 1;
+    unsigned long long bad = 0;
+    int64_t ends[2] = {0, 0};
+    CUDA_OK(cudaMemcpyAsync(&bad, ctx->bad.ptr, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(&ends[0], g.row_ptr.ptr, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(&ends[1], csc::as<int64_t>(g.row_ptr) + n, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    if (bad != 0 || ends[0] != 0 || ends[1] != nnz) {
+      g.loaded = false;
+      return fail(ctx, CSC_EINVAL, "csc_set_graph: malformed CSR (" + std::to_string(bad) +
+                                       " violations)");
+    }
+  }
+  CUDA_OK(csc::launch_graph_prep(g, s));
+  ctx->launches += 1;
+  g.loaded = true;
+  return CSC_OK;
+}
+
+csc_status csc_filter_coeffs(int m, double lambda_c, double* a_out) {
+  if (m < 0 || !a_out || !(lambda_c == lambda_c)) return CSC_EINVAL;
+  coeffs(m, lambda_c, a_out);
+  return CSC_OK;
+}
+
+double csc_count_tolerance(int k, int c) { return c > 0 ? tolerance(k, c) : 0.0; }
+
+csc_status csc_count_from_moments(int m, const double* mu, double lambda_c, int d, int c,
+                                  double* count_out) {
+  if (m < 0 || !mu || d < 1 || c < 1 || !count_out) return CSC_EINVAL;
+  std::vector<double> a(m + 1);
+  coeffs(m, lambda_c, a.data());
+  *count_out = count_moments(m, mu, a.data(), d, c);
+  return CSC_OK;
+}
+
+csc_status csc_lambda_search_moments(int m, const double* mu, int d, int c, int k, double tau,
+                                     double lambda_prev, int max_steps, double* lambda_out,
+                                     double* count_out, int* evals_out) {
+  if (m < 0 || !mu || d < 1 || c < 1 || k < 1 || !(tau >= 0.0) || max_steps < 1 || !lambda_out ||
+      !count_out || !evals_out)
+    return CSC_EINVAL;
+  std::vector<double> a(m + 1);
+  auto count = [&](double lam) {
+    coeffs(m, lam, a.data());
+    return count_moments(m, mu, a.data(), d, c);
+  };
+  search(count, k, tau, lambda_prev, max_steps, lambda_out, count_out, evals_out);
+  return CSC_OK;
+}
+
+csc_status csc_signals(csc_ctx* ctx, uint64_t seed, int64_t n, int64_t col0, int c, int d, void* out,
+                       int dtype, int64_t ld, int where) {
+  if (!ctx) return CSC_EINVAL;
+  if (n < 0 || col0 < 0 || c < 0 || d < 1 || ld < c || !out || !valid_dtype(dtype) || !valid_where(where))
+    return fail(ctx, CSC_EINVAL, "csc_signals: bad arguments");
+  const float inv_sqrt_d = (float)(1.0 / std::sqrt((double)d));
+  cudaStream_t s = ctx->stream;
+  ctx->launches += 1;
+  if (where == CSC_DEVICE) {
+    CUDA_OK(csc::launch_signals(out, dtype, n, c, ld, seed, col0, c, inv_sqrt_d, s));
+    return CSC_OK;
+  }
+  const size_t esz = dtype_size(dtype);
+  ALLOC_OK(csc::ensure(ctx->out_stage, (size_t)std::max<int64_t>(n, 1) * std::max(c, 1) * esz));
+  CUDA_OK(csc::launch_signals(ctx->out_stage.ptr, dtype, n, c, c, seed, col0, c, inv_sqrt_d, s));
+  if (n > 0 && c > 0)
+    CUDA_OK(cudaMemcpy2DAsync(out, ld * esz, ctx->out_stage.ptr, c * esz, c * esz, n,
+                              cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  return CSC_OK;
+}
+
+csc_status csc_cheb_filter(csc_ctx* ctx, int m, double lambda_c, const void* R, int r_dtype, int c,
+                           int64_t ldr, int r_where, float* psi_out, int64_t ldp, int psi_where,
+                           double* mu_out) {
+  if (!ctx) return CSC_EINVAL;
+  if (!ctx->g.loaded) return fail(ctx, CSC_ESTATE, "csc_cheb_filter: no graph loaded");
+  if (m < 1 || c < 1 || !R || ldr < c || !valid_dtype(r_dtype) || !valid_where(r_where) ||
+      !(lambda_c >= 0.0 && lambda_c <= 2.0) || (psi_out && (ldp < c || !valid_where(psi_where))))
+    return fail(ctx, CSC_EINVAL, "csc_cheb_filter: bad arguments");
+  const int64_t n = ctx->g.n;
+  cudaStream_t s = ctx->stream;
+  Source src;
+  src.philox = false;
+  src.dtype = r_dtype;
+  src.d = 1;
+  if (r_where == CSC_HOST) {
+    const size_t esz = dtype_size(r_dtype);
+    ALLOC_OK(csc::ensure(ctx->rstage, (size_t)n * c * esz));
+    CUDA_OK(cudaMemcpy2DAsync(ctx->rstage.ptr, c * esz, R, ldr * esz, c * esz, n,
+                              cudaMemcpyHostToDevice, s));
+    src.R = ctx->rstage.ptr;
+    src.ldr = c;
+  } else {
+    src.R = R;
+    src.ldr = ldr;
+  }
+  const int w = tile_width(ctx, n, c);
+  const int cpad = ((c + w - 1) / w) * w;
+  float* psi = nullptr;
+  if (psi_out) {
+    ALLOC_OK(csc::ensure(ctx->psi, (size_t)n * cpad * 4));
+    psi = csc::as<float>(ctx->psi);
+  }
+  csc_status st = run_filter(ctx, m, lambda_c, c, src, psi, cpad);
+  if (st != CSC_OK) return st;
+  if (psi_out) {
+    const cudaMemcpyKind kind = psi_where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CUDA_OK(cudaMemcpy2DAsync(psi_out, ldp * 4, psi, (size_t)cpad * 4, (size_t)c * 4, n, kind, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+  }
+  if (mu_out) std::copy(ctx->mu.begin(), ctx->mu.end(), mu_out);
+  return CSC_OK;
+}
+
+csc_status csc_estimate_lambda_k(csc_ctx* ctx, int k, int m, int d, uint64_t seed,
+                                 double* lambda_out, double* count_out, int* evals_out) {
+  if (!ctx) return CSC_EINVAL;
+  if (!ctx->g.loaded) return fail(ctx, CSC_ESTATE, "csc_estimate_lambda_k: no graph loaded");
+  if (k < 1 || m < 1 || d < 1) return fail(ctx, CSC_EINVAL, "csc_estimate_lambda_k: bad arguments");
+  Source src;
+  src.seed = seed;
+  src.col0 = ctx->next_id;
+  src.d = d;
+  csc_status st = run_filter(ctx, m, 1.0, d, src, nullptr, 0);
+  if (st != CSC_OK) return st;
+  const double tau = ctx->opts.count_tol > 0 ? ctx->opts.count_tol : tolerance(k, d);
+  double lam, cnt;
+  int evals;
+  search([&](double x) { return count_at(ctx, x, d, d); }, k, tau, -1.0, ctx->opts.max_bisect, &lam,
+         &cnt, &evals);
+  ctx->lambda = lam;
+  ctx->has_lambda = true;
+  if (lambda_out) *lambda_out = lam;
+  if (count_out) *count_out = cnt;
+  if (evals_out) *evals_out = evals;
+  return CSC_OK;
+}
+
+csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k, double lambda_c,
+                      double* lambda_out, double* count_out, int* evals_out, int* cols_out) {
+  if (!ctx) return CSC_EINVAL;
+  if (!ctx->g.loaded) return fail(ctx, CSC_ESTATE, "csc_filter: no graph loaded");
+  if (m < 1 || d < 1 || d > 1024 || !(p >= 0.0 && p < 1.0) || lambda_c > 2.0)
+    return fail(ctx, CSC_EINVAL, "csc_filter: need m >= 1, 1 <= d <= 1024, 0 <= p < 1, lambda_c <= 2");
+  const int64_t n = ctx->g.n;
+  if (ctx->t > 0 && d != ctx->ring_d)
+    return fail(ctx, CSC_EINVAL, "csc_filter: d must stay the same across snapshots");
+  if (lambda_c < 0 && !ctx->has_lambda && k < 1)
+    return fail(ctx, CSC_ESTATE, "csc_filter: no cutoff yet; pass lambda_c >= 0 or k >= 1");
+  cudaStream_t s = ctx->stream;
+  const bool first = ctx->t == 0 || p <= 0.0;
+  std::vector<int> slots;
+  if (first) {
+    for (int q = 0; q < d; ++q) slots.push_back(q);
+  } else {
+    const int dp = (int)std::floor(p * d);
+    const int c = d - dp;
+    std::vector<int> order(d);
+    for (int q = 0; q < d; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return ctx->stamp[x] < ctx->stamp[y]; });
+    slots.assign(order.begin(), order.begin() + c);
+    std::sort(slots.begin(), slots.end());
+  }
+  const int c = (int)slots.size();
+  Source src;
+  src.seed = seed;
+  src.col0 = ctx->next_id;
+  src.d = d;
+  double lam = lambda_c;
+  int evals = 0;
+  bool searched = false;
+  const double tau = ctx->opts.count_tol > 0 ? ctx->opts.count_tol : (k >= 1 ? tolerance(k, c) : 0.0);
+  if (lam < 0 && !ctx->has_lambda) {
+    csc_status st = run_filter(ctx, m, 1.0, c, src, nullptr, 0);
+    if (st != CSC_OK) return st;
+    double cnt;
+    search([&](double x) { return count_at(ctx, x, d, c); }, k, tau, -1.0, ctx->opts.max_bisect,
+           &lam, &cnt, &evals);
+    searched = true;
+  } else if (lam < 0) {
+    lam = ctx->lambda;
+  }
+  const int w = tile_width(ctx, n, c);
+  const int cpad = ((c + w - 1) / w) * w;
+  ALLOC_OK(csc::ensure(ctx->psi, (size_t)n * cpad * 4));
+  csc_status st = run_filter(ctx, m, lam, c, src, csc::as<float>(ctx->psi), cpad);
+  if (st != CSC_OK) return st;
+  double cnt = count_at(ctx, lam, d, c);
+  if (lambda_c < 0 && k >= 1 && !searched) {
+    double lam2, cnt2;
+    search([&](double x) { return count_at(ctx, x, d, c); }, k, tau, lam, ctx->opts.max_bisect, &lam2,
+           &cnt2, &evals);
+    if (lam2 != lam) {
+      st = run_filter(ctx, m, lam2, c, src, csc::as<float>(ctx->psi), cpad);
+      if (st != CSC_OK) return st;
+      lam = lam2;
+    }
+    cnt = cnt2;
+  }
+  // splice the new columns into the oldest slots and row-normalise (Eq. 6)
+  if (ctx->t == 0) {
+    ALLOC_OK(csc::ensure(ctx->theta, (size_t)n * d * 4));
+    ALLOC_OK(csc::ensure(ctx->y, (size_t)n * d * 4));
+    ALLOC_OK(csc::ensure(ctx->slot_src, (size_t)d * 4));
+    ctx->stamp.assign(d, 0);
+    ctx->ring_n = n;
+    ctx->ring_d = d;
+  }
+  std::vector<int> src_of(d, -1);
+  for (int v = 0; v < c; ++v) src_of[slots[v]] = v;
+  CUDA_OK(cudaMemcpyAsync(ctx->slot_src.ptr, src_of.data(), d * 4, cudaMemcpyHostToDevice, s));
+  CUDA_OK(csc::launch_assemble(csc::as<float>(ctx->theta), d, csc::as<float>(ctx->psi), cpad,
+                               csc::as<int>(ctx->slot_src), d, ctx->y.ptr, ctx->opts.precision, d, n,
+                               s));
+  ctx->launches += 1;
+  CUDA_OK(cudaStreamSynchronize(s));
+  ctx->t += 1;
+  for (int q : slots) ctx->stamp[q] = ctx->t;
+  ctx->next_id += c;
+  ctx->lambda = lam;
+  ctx->has_lambda = true;
+  if (lambda_out) *lambda_out = lam;
+  if (count_out) *count_out = cnt;
+  if (evals_out) *evals_out = evals;
+  if (cols_out) *cols_out = c;
+  return CSC_OK;
+}
+
+csc_status csc_get_features(csc_ctx* ctx, void* dst, int dtype, int64_t ld, int normalized, int where) {
+  if (!ctx) return CSC_EINVAL;
+  if (ctx->t == 0) return fail(ctx, CSC_ESTATE, "csc_get_features: nothing filtered yet");
+  if (!dst || !valid_dtype(dtype) || ld < ctx->ring_d || !valid_where(where))
+    return fail(ctx, CSC_EINVAL, "csc_get_features: bad arguments");
+  if (normalized)
+    return copy_out(ctx, ctx->y.ptr, ctx->opts.precision, ctx->ring_d, ctx->ring_n, ctx->ring_d, dst,
+                    dtype, ld, where);
+  return copy_out(ctx, ctx->theta.ptr, CSC_F32, ctx->ring_d, ctx->ring_n, ctx->ring_d, dst, dtype, ld,
+                  where);
+}
+
+csc_status csc_get_moments(csc_ctx* ctx, double* mu_out, int len) {
+  if (!ctx) return CSC_EINVAL;
+  if (ctx->mu.empty()) return fail(ctx, CSC_ESTATE, "csc_get_moments: no filtering pass yet");
+  if (!mu_out || len < 0 || len > (int)ctx->mu.size())
+    return fail(ctx, CSC_EINVAL, "csc_get_moments: len must be <= 2m+1");
+  std::copy(ctx->mu.begin(), ctx->mu.begin() + len, mu_out);
+  return CSC_OK;
+}
+
+csc_status csc_kmeans(csc_ctx* ctx, const void* Y, int y_dtype, int64_t n, int d, int64_t ldy,
+                      int y_where, int k, const int64_t* init_idx, const int32_t* prev_assign,
+                      int max_iter, int32_t* assign_out, int assign_where, double* centroids_out,
+                      double* inertia_out, int* iters_out) {
+  if (!ctx) return CSC_EINVAL;
+  if (!Y || n < 1 || d < 1 || ldy < d || k < 1 || k > n || !init_idx || !assign_out ||
+      !valid_dtype(y_dtype) || !valid_where(y_where) || !valid_where(assign_where))
+    return fail(ctx, CSC_EINVAL, "csc_kmeans: bad arguments");
+  for (int j = 0; j < k; ++j)
+    if (init_idx[j] < 0 || init_idx[j] >= n) return fail(ctx, CSC_EINVAL, "csc_kmeans: init_idx out of range");
+  cudaStream_t s = ctx->stream;
+  const size_t esz = dtype_size(y_dtype);
+  const void* ydev = Y;
+  int64_t ld = ldy;
+  if (y_where == CSC_HOST) {
+    ALLOC_OK(csc::ensure(ctx->ystage, (size_t)n * d * esz));
+    CUDA_OK(cudaMemcpy2DAsync(ctx->ystage.ptr, d * esz, Y, ldy * esz, d * esz, n,
+                              cudaMemcpyHostToDevice, s));
+    ydev = ctx->ystage.ptr;
+    ld = d;
+  }
+  const int32_t* prev = nullptr;
+  if (prev_assign) {
+    if (assign_where == CSC_HOST) {
+      for (int64_t i = 0; i < n; ++i)
+        if (prev_assign[i] < 0 || prev_assign[i] >= k)
+          return fail(ctx, CSC_EINVAL, "csc_kmeans: prev_assign out of range");
+      ALLOC_OK(csc::ensure(ctx->astage, (size_t)n * 4));
+      CUDA_OK(cudaMemcpyAsync(ctx->astage.ptr, prev_assign, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+      prev = csc::as<int32_t>(ctx->astage);
+    } else {
+      prev = prev_assign;
+    }
+  }
+  csc::KmeansResult res;
+  csc_status st = csc::kmeans_run(ctx->km, ydev, y_dtype, n, d, ld, k, init_idx, prev,
+                                  max_iter > 0 ? max_iter : ctx->opts.max_iter, s, &res, &ctx->err);
+  ctx->launches += res.launches;
+  if (st != CSC_OK) return st;
+  const cudaMemcpyKind kind = assign_where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CUDA_OK(cudaMemcpyAsync(assign_out, res.assign, (size_t)n * 4, kind, s));
+  if (centroids_out)
+    CUDA_OK(cudaMemcpyAsync(centroids_out, ctx->km.c64.ptr, (size_t)k * d * 8, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (inertia_out) *inertia_out = res.inertia;
+  if (iters_out) *iters_out = res.iters;
+  return CSC_OK;
+}
+
+csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_idx, int32_t* assign_out,
+                       int where, double* cost_out, int* iters_out) {
+  if (!ctx) return CSC_EINVAL;
+  if (ctx->t == 0) return fail(ctx, CSC_ESTATE, "csc_cluster: call csc_filter first");
+  const int64_t n = ctx->ring_n;
+  const int d = ctx->ring_d;
+  if (k < 1 || k > n || !assign_out || !valid_where(where))
+    return fail(ctx, CSC_EINVAL, "csc_cluster: bad arguments");
+  std::vector<int64_t> idx;
+  if (init_idx) {
+    idx.assign(init_idx, init_idx + k);
+    for (int64_t v : idx)
+      if (v < 0 || v >= n) return fail(ctx, CSC_EINVAL, "csc_cluster: init_idx out of range");
+  } else {
+    idx = forgy_draw(seed ^ ((uint64_t)ctx->t * 0x9E3779B97F4A7C15ull), n, k);
+  }
+  cudaStream_t s = ctx->stream;
+  const bool warm = ctx->has_prev && ctx->prev_k == k;
+  csc::KmeansResult res;
+  csc_status st = csc::kmeans_run(ctx->km, ctx->y.ptr, ctx->opts.precision, n, d, d, k, idx.data(),
+                                  warm ? csc::as<int32_t>(ctx->prev_assign) : nullptr,
+                                  ctx->opts.max_iter, s, &res, &ctx->err);
+  ctx->launches += res.launches;
+  if (st != CSC_OK) return st;
+  ALLOC_OK(csc::ensure(ctx->prev_assign, (size_t)n * 4));
+  CUDA_OK(cudaMemcpyAsync(ctx->prev_assign.ptr, res.assign, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  const cudaMemcpyKind kind = where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CUDA_OK(cudaMemcpyAsync(assign_out, res.assign, (size_t)n * 4, kind, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  ctx->has_prev = true;
+  ctx->prev_k = k;
+  if (cost_out) *cost_out = std::sqrt(std::max(0.0, res.inertia));
+  if (iters_out) *iters_out = res.iters;
+  return CSC_OK;
+}
+
+}  // extern "C"

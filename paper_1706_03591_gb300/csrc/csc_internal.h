@@ -1,0 +1,134 @@
+// Internal declarations shared by the CUDA translation units of libcsc.
+// Not part of the ABI (see include/csc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/csc.h"
+
+namespace csc {
+
+// ------------------------------------------------------------------ device buffers
+
+// Grow-only device allocation owned by a context.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Returns false (and leaves the buffer empty) when cudaMalloc fails.
+bool ensure(DevBuf& b, size_t bytes);
+void release(DevBuf& b);
+
+template <typename T>
+inline T* as(DevBuf& b) { return static_cast<T*>(b.ptr); }
+
+// ------------------------------------------------------------------ graph state
+
+struct Graph {
+  int64_t n = 0, nnz = 0;
+  bool weighted = false;
+  DevBuf row_ptr;   // int64[n+1]
+  DevBuf col;       // int32[nnz]
+  DevBuf val;       // float[nnz] (weighted only)
+  DevBuf scale;     // float[n], D^{-1/2} (0 for isolated nodes)
+  DevBuf deg;       // double[n]
+  bool loaded = false;
+};
+
+// ------------------------------------------------------------------ launch helpers
+
+int num_sms();
+int grid_for(const void* kernel, int block, size_t smem = 0);
+
+// ------------------------------------------------------------------ graph kernels (graph.cu)
+
+cudaError_t launch_graph_prep(const Graph& g, cudaStream_t s);
+// Device-side CSR validation; writes the number of violations into *bad (device int64).
+cudaError_t launch_graph_check(const Graph& g, unsigned long long* bad, cudaStream_t s);
+
+// ------------------------------------------------------------------ signals (signals.cu)
+
+// Fills an n x w block (leading dimension w) of tile columns [col0, col0 + valid) of the
+// Philox N(0, 1/d) signals; columns >= valid are zero.  dtype CSC_F32 / CSC_BF16.
+cudaError_t launch_signals(void* out, int dtype, int64_t n, int w, int64_t ld, uint64_t seed,
+                           int64_t col0, int valid, float inv_sqrt_d, cudaStream_t s);
+// Copies columns [c0, c0 + valid) of a caller block (n x ld_src, dtype) into an n x w
+// tile buffer of the same dtype, zero-filling columns >= valid.
+cudaError_t launch_copy_tile(void* dst, const void* src, int dtype, int64_t n, int w,
+                             int64_t ld_src, int c0, int valid, cudaStream_t s);
+
+// ------------------------------------------------------------------ Chebyshev recursion (cheb.cu)
+
+struct StepArgs {
+  int64_t n;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const float* val;     // nullptr: unit weights
+  const float* scale;   // D^{-1/2}
+  const void* tg;       // gathered block T_j (n x w)
+  const void* tp;       // T_{j-1} (own rows), unused on the first step
+  float* tn;            // T_{j+1} (n x w)
+  float* psi;           // Psi rows base (nullptr: moments only)
+  int64_t ldp;          // Psi leading dimension
+  const float* coef;    // device coefficients a_0..a_m (float32)
+  int j;                // this step produces T_{j+1}
+  double* part;         // block partial sums of this step, [nq][grid]
+  int w;                // tile width (= 4 * lanes per row)
+};
+
+// First step: T_1 = L~ T_0, Psi = a_0 T_0 + a_1 T_1, partials {<T0,T0>, <T1,T1>, <T1,T0>}.
+cudaError_t launch_cheb_first(const StepArgs& a, int t0_dtype, int grid, cudaStream_t s);
+// General step: T_{j+1} = 2 L~ T_j - T_{j-1}, Psi += a_{j+1} T_{j+1}, partials
+// {<T_{j+1},T_{j+1}>, <T_{j+1},T_j>}.  tp_dtype is the storage type of T_{j-1}.
+cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStream_t s);
+int cheb_grid(int w);
+// Sums partials[(q * nslots + slot) * grid + b] over b (fixed order) into out[q * nslots + slot]
+// for q in 0..nq-1, accumulating across `tiles` consecutive partial blocks of stride tile_stride.
+cudaError_t launch_reduce_partials(const double* part, int nrows, int grid, int tiles,
+                                   int64_t tile_stride, double* out, cudaStream_t s);
+
+// ------------------------------------------------------------------ features (features.cu)
+
+// Splice + row normalisation: for each row, ring slot q takes psi[row*ldp + src[q]] when
+// src[q] >= 0 (and is written back to theta), else keeps theta; y = theta / ||theta||.
+cudaError_t launch_assemble(float* theta, int64_t ldt, const float* psi, int64_t ldp,
+                            const int* src, int d, void* y, int y_dtype, int64_t ldy, int64_t n,
+                            cudaStream_t s);
+// Copies an n x d block (src dtype float or bf16, ld_src) to dst (dtype, ld_dst) on device.
+cudaError_t launch_convert(const void* src, int src_dtype, int64_t ld_src, void* dst,
+                           int dst_dtype, int64_t ld_dst, int64_t n, int d, cudaStream_t s);
+
+// ------------------------------------------------------------------ k-means (kmeans.cu)
+
+struct KmeansState {
+  DevBuf c64, c32, cn2, cmax;   // centroids float64 [k][dp], float32 [kp][dp], |c|^2 [kp], max|c|
+  DevBuf sums, counts;          // int64 [k][dp], int32 [k]
+  DevBuf assign_a, assign_b;    // int32 [n]
+  DevBuf flagged, counters;     // int32 [n]; unsigned long long [4]
+  DevBuf maxabs;                // float bits (uint32)
+  DevBuf inertia_part;          // double [grid]
+  DevBuf init_idx;              // int64 [k]
+};
+
+struct KmeansResult {
+  int iters = 0;
+  bool converged = false;
+  double inertia = 0.0;
+  int32_t* assign = nullptr;   // device pointer to the final assignment (inside the state)
+  int64_t launches = 0;        // kernels launched
+};
+
+// Runs Lloyd's iteration on device features y (n x d, leading dimension ldy, dtype).
+// init_idx: host int64[k]; prev_assign: device int32[n] or nullptr.
+csc_status kmeans_run(KmeansState& st, const void* y, int y_dtype, int64_t n, int d, int64_t ldy,
+                      int k, const int64_t* init_idx, const int32_t* prev_assign, int max_iter,
+                      cudaStream_t s, KmeansResult* res, std::string* err);
+void kmeans_release(KmeansState& st);
+
+}  // namespace csc

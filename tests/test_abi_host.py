@@ -1,0 +1,101 @@
+"""The C-ABI library on the CPU: it builds, loads, exports every symbol of
+include/csc.h, and its host-only helpers (no GPU work) agree with the oracle."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import ROOT
+from oracle import chebyshev as cb
+from oracle import laplacian as lp
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1706_03591_gb300 import build
+    build.build()
+    import paper_1706_03591_gb300 as csc
+    return csc
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "csc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(csc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(lib):
+    from paper_1706_03591_gb300 import _abi
+    so = ctypes.CDLL(_abi.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 19
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    # the binding declares exactly the header's entry points
+    assert sorted(_abi.SIGNATURES) == names
+    assert lib.csc_abi_version() == 1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1706_03591_gb300 import _abi
+    with pytest.raises(RuntimeError, match="not found"):
+        _abi.load(str(tmp_path / "libcsc.so"))
+
+
+def test_coefficients_match_oracle(lib):
+    for m in (1, 2, 10, 50, 100):
+        for lam in (0.0, 0.17, 0.5, 1.0, 1.33, 2.0, 2.5, -0.3):
+            a = lib.csc_filter_coeffs(m, lam)
+            ref = cb.filter_coefficients(m, min(2.0, max(0.0, lam)))
+            np.testing.assert_allclose(a, ref, rtol=0, atol=1e-15)
+
+
+def test_tolerance_matches_oracle(lib):
+    for k, c in ((10, 64), (10, 32), (100, 64), (1, 1000), (64, 39)):
+        assert lib.csc_count_tolerance(k, c) == cb.count_tolerance(k, c)
+
+
+def _moments_case(seed=3, n=400, c=12, d=24, m=40):
+    g = W.sbm_graph(n, 5, 14, 10, seed=seed)
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    r = W.gaussian_block(n, c, d, seed=seed + 1).astype(np.float64)
+    return lt, r, cb.moments(lt, r, 2 * m), cb.cheb_basis(lt, r, m), d, c, m
+
+
+def test_count_from_moments_equals_direct_eigencount(lib):
+    lt, r, mu, basis, d, c, m = _moments_case()
+    for lam in (0.2, 0.55, 0.9, 1.5):
+        direct = cb.eigencount(cb.combine(basis, cb.filter_coefficients(m, lam)), d)
+        assert lib.csc_count_from_moments(m, mu, lam, d, c) == pytest.approx(direct, rel=1e-9)
+
+
+def test_lambda_search_matches_oracle_control_flow(lib):
+    lt, r, mu, basis, d, c, m = _moments_case()
+
+    def direct(lam):
+        return cb.eigencount(cb.combine(basis, cb.filter_coefficients(m, lam)), d)
+
+    for k in (3, 5, 8, 15):
+        tau = cb.count_tolerance(k, c)
+        for prev in (None, 0.05, 0.4, 1.2, 1.95):
+            ref = cb.lambda_search(direct, k, tau, prev, 30)
+            got = lib.csc_lambda_search_moments(m, mu, d, c, k, tau, -1.0 if prev is None else prev, 30)
+            # same decisions -> the same cutoff bit for bit unless a count sits on a threshold
+            assert got[2] == ref[2], (k, prev, got, ref)
+            assert got[0] == ref[0], (k, prev, got, ref)
+            assert got[1] == pytest.approx(ref[1], rel=1e-9)
+
+
+def test_lambda_search_cap_and_bad_args(lib):
+    m = 4
+    mu = np.zeros(2 * m + 1)
+    lam, cnt, ev = lib.csc_lambda_search_moments(m, mu, 8, 8, 3, 0.5, -1.0, 7)
+    assert ev == 7 and cnt == 0.0 and lam == 2.0 - 2.0**-6
+    with pytest.raises(lib.CscError):
+        lib.csc_lambda_search_moments(m, mu, 8, 8, 0, 0.5, -1.0, 7)
+    with pytest.raises(lib.CscError):
+        lib.csc_filter_coeffs(-1, 0.5)

@@ -1,0 +1,285 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: features within 1e-5 relative Frobenius error (float32 storage)
+and 3e-3 against the float64-signal oracle for bfloat16 signal storage;
+moments within 1e-5 of mu_0; k-means assignments exactly equal given identical
+features and initial rows.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import chebyshev as cb
+from oracle import kmeans as km
+from oracle import laplacian as lp
+from oracle.dynamic import DynamicCSC, row_normalize
+from oracle.philox import gaussian_columns
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+BF16_TOL = 3e-3
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def upload_graph(ctx, g, vals=None):
+    ctx.set_graph(g.n, dev(g.row_ptr), dev(g.col_idx), None if vals is None else dev(vals))
+
+
+@pytest.fixture(scope="module")
+def cfg1_graph():
+    return W.sbm_graph(2000, 10, 20, 10, seed=1)
+
+
+def test_signals_match_oracle_generator(gpu_lib):
+    n, c, d, col0, seed = 5003, 13, 64, 7, 0xDEADBEEF12345
+    with gpu_lib.Context() as ctx:
+        out = torch.zeros((n, c), dtype=torch.float32, device="cuda")
+        ctx.signals(seed, n, col0, c, d, out)
+        ref = gaussian_columns(seed, n, np.arange(col0, col0 + c), d)
+        got = out.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+        outb = torch.zeros((n, 16), dtype=torch.bfloat16, device="cuda")
+        ctx.signals(seed, n, col0, c, d, outb[:, :c])
+        gb = outb[:, :c].float().cpu().numpy()
+        # bf16 rounding of the float32 draws: within one bf16 ulp of the float64 draw
+        assert np.all(np.abs(gb - ref) <= 2.0**-7 * np.abs(ref) + 1e-30)
+        assert np.all(outb[:, c:].float().cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("c", [64, 13, 1])
+def test_cheb_filter_parity_tiles(gpu_lib, cfg1_graph, tile, c):
+    g = cfg1_graph
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    r = W.gaussian_block(g.n, c, 64, seed=c * 7 + tile)
+    m, lam = 50, 0.53
+    with gpu_lib.Context({"col_tile": tile}) as ctx:
+        upload_graph(ctx, g)
+        psi = torch.zeros((g.n, c), dtype=torch.float32, device="cuda")
+        mu = ctx.cheb_filter(m, lam, dev(r), psi)
+    ref = cb.cheb_filter(lt, r.astype(np.float64), m, lam)
+    assert rel(psi.cpu().numpy(), ref) < FP32_TOL
+    mu_ref = cb.moments(lt, r.astype(np.float64), 2 * m)
+    assert np.max(np.abs(mu - mu_ref)) < FP32_TOL * mu_ref[0]
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 100])
+def test_cheb_filter_orders(gpu_lib, cfg1_graph, m):
+    g = cfg1_graph
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    r = W.gaussian_block(g.n, 24, 24, seed=m)
+    with gpu_lib.Context() as ctx:
+        upload_graph(ctx, g)
+        psi = np.zeros((g.n, 24), dtype=np.float32)     # host output buffer
+        mu = ctx.cheb_filter(m, 1.1, r, psi)           # host input block
+    assert rel(psi, cb.cheb_filter(lt, r.astype(np.float64), m, 1.1)) < FP32_TOL
+    mu_ref = cb.moments(lt, r.astype(np.float64), 2 * m)
+    assert np.max(np.abs(mu - mu_ref)) < FP32_TOL * mu_ref[0]
+
+
+def test_cheb_filter_weighted_and_isolated(gpu_lib):
+    g = W.random_csr(3001, 9, seed=4, isolated=40)
+    rng = np.random.default_rng(0)
+    upper_w = rng.uniform(0.1, 3.0, g.nnz)
+    # symmetric weights: weight of (u,v) equals weight of (v,u)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    key_lo = np.minimum(rows, g.col_idx) * g.n + np.maximum(rows, g.col_idx)
+    _, inv = np.unique(key_lo, return_inverse=True)
+    vals = upper_w[inv].astype(np.float32)
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx, vals)
+    r = W.gaussian_block(g.n, 20, 32, seed=2)
+    with gpu_lib.Context({"col_tile": 16}) as ctx:
+        upload_graph(ctx, g, vals)
+        psi = torch.zeros((g.n, 20), device="cuda")
+        ctx.cheb_filter(40, 0.8, dev(r), psi)
+    assert rel(psi.cpu().numpy(), cb.cheb_filter(lt, r.astype(np.float64), 40, 0.8)) < FP32_TOL
+
+
+def test_cheb_filter_edgeless_graph(gpu_lib):
+    n = 257
+    g_rp = np.zeros(n + 1, dtype=np.int64)
+    g_ci = np.zeros(0, dtype=np.int32)
+    r = W.gaussian_block(n, 5, 5, seed=1)
+    m, lam = 7, 0.9
+    with gpu_lib.Context() as ctx:
+        ctx.set_graph(n, g_rp, g_ci)
+        psi = np.zeros((n, 5), dtype=np.float32)
+        ctx.cheb_filter(m, lam, r, psi)
+    a = cb.filter_coefficients(m, lam)
+    # every node isolated: T_j(0) = cos(j pi / 2) -> h(1) = a0 - a2 + a4 - a6
+    expect = (a[0] - a[2] + a[4] - a[6]) * r.astype(np.float64)
+    np.testing.assert_allclose(psi, expect, rtol=2e-6, atol=1e-7)
+
+
+def test_cheb_filter_bf16_signals(gpu_lib, cfg1_graph):
+    g = cfg1_graph
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    r = W.gaussian_block(g.n, 64, 64, seed=5)
+    rb = torch.from_numpy(r).to(torch.bfloat16)
+    r_widened = rb.float().numpy().astype(np.float64)   # the exact stored values
+    with gpu_lib.Context() as ctx:
+        upload_graph(ctx, g)
+        psi = torch.zeros((g.n, 64), device="cuda")
+        ctx.cheb_filter(50, 0.53, rb.cuda(), psi)
+    got = psi.cpu().numpy()
+    assert rel(got, cb.cheb_filter(lt, r_widened, 50, 0.53)) < FP32_TOL
+    err_fp64_signals = rel(got, cb.cheb_filter(lt, r.astype(np.float64), 50, 0.53))
+    assert err_fp64_signals < BF16_TOL
+
+
+def test_estimate_lambda_matches_oracle_dichotomy(gpu_lib, cfg1_graph):
+    g = cfg1_graph
+    k, m, d, seed = 10, 50, 64, 99
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    basis = cb.cheb_basis(lt, gaussian_columns(seed, g.n, np.arange(d), d), m)
+
+    def count(lam):
+        return cb.eigencount(cb.combine(basis, cb.filter_coefficients(m, lam)), d)
+
+    lam_ref, cnt_ref, ev_ref = cb.lambda_search(count, k, cb.count_tolerance(k, d), None, 30)
+    with gpu_lib.Context() as ctx:
+        upload_graph(ctx, g)
+        lam, cnt, ev = ctx.estimate_lambda_k(k, m, d, seed)
+    assert (lam, ev) == (lam_ref, ev_ref)
+    assert cnt == pytest.approx(cnt_ref, rel=1e-4)
+
+
+def _kmeans_case(n, d, k, seed, dtype=np.float32):
+    y, _ = W.clustered_points(n, d, k, seed=seed, spread=0.6)
+    return y.astype(dtype), W.forgy_indices(n, k, seed=seed + 1)
+
+
+@pytest.mark.parametrize("n,d,k", [(20000, 64, 10), (20011, 37, 100), (5000, 256, 100), (777, 8, 3)])
+def test_kmeans_exact_assignments(gpu_lib, n, d, k):
+    y, idx = _kmeans_case(n, d, k, seed=n + d)
+    lab_ref, c_ref, it_ref, conv_ref = km.lloyd(y, km.forgy_centroids(y, idx), max_iter=100)
+    with gpu_lib.Context() as ctx:
+        out = ctx.kmeans(dev(y), k, idx, max_iter=100, assign_out=torch.zeros(n, dtype=torch.int32,
+                                                                               device="cuda"))
+    assign = out["assign"].cpu().numpy()
+    np.testing.assert_array_equal(assign, lab_ref)
+    assert out["iters"] == it_ref
+    np.testing.assert_allclose(out["centroids"], c_ref, rtol=0, atol=1e-12)
+    assert out["inertia"] == pytest.approx(km.inertia(y, lab_ref, c_ref), rel=1e-5)
+
+
+def test_kmeans_warm_start_and_bf16(gpu_lib):
+    n, d, k = 9000, 48, 12
+    y, idx = _kmeans_case(n, d, k, seed=3)
+    prev = np.random.default_rng(1).integers(0, k, n).astype(np.int32)
+    prev[:k] = np.arange(k)
+    prev[prev == 5] = 4                       # cluster 5 empty -> takes row idx[5]
+    lab_ref, c_ref, it_ref, _ = km.lloyd(y, km.warm_centroids(y, prev, idx), max_iter=100)
+    with gpu_lib.Context() as ctx:
+        out = ctx.kmeans(y, k, idx, prev_assign=prev, max_iter=100)
+    np.testing.assert_array_equal(out["assign"], lab_ref)
+    assert out["iters"] == it_ref
+    yb = torch.from_numpy(y).to(torch.bfloat16)
+    yw = yb.float().numpy()
+    lab_b, _, it_b, _ = km.lloyd(yw, km.forgy_centroids(yw, idx), max_iter=100)
+    with gpu_lib.Context() as ctx:
+        out = ctx.kmeans(yb.cuda(), k, idx, max_iter=100)
+    np.testing.assert_array_equal(out["assign"], lab_b)
+    assert out["iters"] == it_b
+
+
+def test_kmeans_exact_ties_lowest_index(gpu_lib):
+    # duplicated centroid rows make every distance to centroids 0 and 1 exactly equal
+    y, _ = W.clustered_points(3000, 16, 4, seed=6)
+    y[1] = y[0]
+    idx = np.array([0, 1, 2, 3])
+    lab_ref, _, it_ref, _ = km.lloyd(y, km.forgy_centroids(y, idx), max_iter=3)
+    with gpu_lib.Context() as ctx:
+        out = ctx.kmeans(y, 4, idx, max_iter=3)
+    np.testing.assert_array_equal(out["assign"], lab_ref)
+
+
+def test_algorithm1_dynamic_parity_cfg1(gpu_lib, cfg1_graph):
+    """SBM n=2000, k=10, degree 20, d=64, m=50, 1% rewiring per step, p=0.5: 1 + 5 snapshots."""
+    n, k, d, m, p, seed = 2000, 10, 64, 50, 0.5, 2024
+    graphs = [cfg1_graph]
+    for t in range(5):
+        graphs.append(W.edge_redraw(graphs[-1], 0.01, seed=100 + t))
+    oracle = DynamicCSC(n, k, d, p, m, seed)
+    with gpu_lib.Context() as ctx:
+        assign = torch.zeros(n, dtype=torch.int32, device="cuda")
+        for t, g in enumerate(graphs):
+            idx = W.forgy_indices(n, k, seed=500 + t)
+            lab_ref = oracle.step(g.row_ptr, g.col_idx, init_idx=idx)
+            h = oracle.history[-1]
+            upload_graph(ctx, g)
+            lam, cnt, ev, cols = ctx.filter(m, d, p, seed, k)
+            cost, iters = ctx.cluster(k, seed, idx, assign)
+            assert cols == h["c"]
+            assert lam == h["lam"], (t, lam, h)
+            assert ev == h["evals"], (t, ev, h)
+            assert cnt == pytest.approx(h["count"], rel=1e-4)
+            theta = np.zeros((n, d), dtype=np.float32)
+            ctx.get_features(theta)
+            assert rel(theta, oracle.features()) < FP32_TOL
+            y = np.zeros((n, d), dtype=np.float32)
+            ctx.get_features(y, normalized=True)
+            assert rel(y, row_normalize(oracle.features())) < FP32_TOL
+            np.testing.assert_array_equal(assign.cpu().numpy(), lab_ref)
+            assert iters == h["passes"]
+            assert cost == pytest.approx(math.sqrt(h["inertia"]), rel=1e-5)
+
+
+def test_full_size_sampled_columns(gpu_lib):
+    """n = 1e6 Zipf SBM (degree 30), 64 columns, m = 100 in the bench's tile configuration;
+    the oracle recomputes two sampled columns in float64 (columns are independent)."""
+    sizes = W.zipf_block_sizes(1_000_000, 100, 0.8)
+    g = W.sbm_graph(1_000_000, sizes, 30, 10, seed=2)
+    c, d, m, lam = 64, 256, 100, 0.06
+    r = W.gaussian_block(g.n, c, d, seed=77)
+    with gpu_lib.Context() as ctx:
+        upload_graph(ctx, g)
+        psi = torch.zeros((g.n, c), device="cuda")
+        mu = ctx.cheb_filter(m, lam, dev(r), psi)
+        got = psi.cpu().numpy()
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    cols = [0, 37]
+    ref = cb.cheb_filter(lt, r[:, cols].astype(np.float64), m, lam)
+    assert rel(got[:, cols], ref) < FP32_TOL
+    # moment identity at full size: ||Psi||_F^2 from the moments equals the direct norm
+    a = cb.filter_coefficients(m, lam)
+    i, j = np.meshgrid(np.arange(m + 1), np.arange(m + 1), indexing="ij")
+    via = float(np.sum(a[i] * a[j] * (mu[i + j] + mu[np.abs(i - j)]) / 2.0))
+    assert abs(via - float(np.sum(got.astype(np.float64) ** 2))) < 1e-5 * mu[0]
+
+
+def test_errors_and_call_order(gpu_lib):
+    with gpu_lib.Context() as ctx:
+        with pytest.raises(gpu_lib.CscError) as e:
+            ctx.filter(10, 8, 0.0, 1, 2)
+        assert e.value.status == 5  # CSC_ESTATE: no graph
+        with pytest.raises(gpu_lib.CscError):
+            ctx.set_graph(3, np.array([0, 1, 2, 2], dtype=np.int64), np.array([0, 0], dtype=np.int32))
+        assert "self-loop" in ctx.last_error
+        with pytest.raises(gpu_lib.CscError):
+            ctx.set_graph(3, np.array([0, 1, 2, 2], dtype=np.int64), np.array([5, 0], dtype=np.int32))
+        ctx.set_graph(3, np.array([0, 1, 2, 2], dtype=np.int64), np.array([1, 0], dtype=np.int32))
+        with pytest.raises(gpu_lib.CscError) as e:
+            ctx.cluster(2, 1, None, np.zeros(3, dtype=np.int32))
+        assert e.value.status == 5
+    with gpu_lib.Context({"checked": 1}) as ctx:
+        with pytest.raises(gpu_lib.CscError):
+            ctx.set_graph(3, dev(np.array([0, 1, 2, 2], dtype=np.int64)),
+                          dev(np.array([5, 0], dtype=np.int32)))  # column out of range
+        assert "malformed" in ctx.last_error
