@@ -262,6 +262,7 @@ def run_ours(a, rank, world, local):
         units = 0.0
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        marks = []
         info = []
         for t, (rp, ci) in enumerate(graphs):
             if t == timed_from:
@@ -270,23 +271,34 @@ def run_ours(a, rank, world, local):
                 torch.cuda.synchronize()
                 clocks.start()
                 e0.record(stream)
+            ev_t = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev_t[0].record(stream)
             ctx.set_graph(N_NODES, rp, ci)
+            ev_t[1].record(stream)
             lam, cnt, ev, cols = ctx.filter(M_ORDER, D_SIG, P_REUSE, seed, K_CLUST)
+            ev_t[2].record(stream)
             cost, iters = ctx.cluster(K_CLUST, seed, inits[t], assign)
+            ev_t[3].record(stream)
             if t >= timed_from:
+                marks.append(ev_t)
                 units += snaps[t].nnz * cols * M_ORDER
                 info.append(dict(lam=lam, count=cnt, evals=ev, cols=cols, iters=iters))
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
         dist.barrier()
-        return e0.elapsed_time(e1), units, info, clk
+        phases = {name: sum(m[i].elapsed_time(m[i + 1]) for m in marks) / max(1, len(marks))
+                  for i, name in enumerate(("set_graph", "filter", "cluster"))}
+        for i, ph in zip(info, marks):
+            i["filter_ms"] = ph[1].elapsed_time(ph[2])
+            i["cluster_ms"] = ph[2].elapsed_time(ph[3])
+        return e0.elapsed_time(e1), units, info, clk, phases
 
     clocks = Clocks(local)
     opts = {"timing": 1, "col_tile": a.tile}
     ctx = csc.Context(opts)
     assign = torch.zeros(N_NODES, dtype=torch.int32, device="cuda")
-    ms, units, info, clk = run_sequence(ctx, dev_graphs, assign, a.warmup)
+    ms, units, info, clk, phases = run_sequence(ctx, dev_graphs, assign, a.warmup)
     stats = ctx.stats()
     tile = int(stats["tile"])
     ctx.close()
@@ -300,7 +312,7 @@ def run_ours(a, rank, world, local):
                        for g in snaps]
         assign_h = torch.zeros(N_NODES, dtype=torch.int32).pin_memory()
         ctx2 = csc.Context(opts)
-        ms2, units2, _, _ = run_sequence(ctx2, host_graphs, assign_h, a.warmup)
+        ms2, units2, _, _, _ = run_sequence(ctx2, host_graphs, assign_h, a.warmup)
         ctx2.close()
         ms2_max = dist.reduce(ms2, "max")
         units2_all = dist.reduce(units2, "sum")
@@ -335,6 +347,7 @@ def run_ours(a, rank, world, local):
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": stats["launches"],
+        "phase_ms": phases,
         "per_step": {"lambda": [i["lam"] for i in info], "evals": [i["evals"] for i in info],
                      "kmeans_iters": [i["iters"] for i in info]},
     }

@@ -7,11 +7,11 @@
  * signals d, the reuse fraction p and k in; assignments X_t out):
  *
  *   csc_set_graph        G_t as CSR                                  Section 2.1, Section 4
- *   csc_estimate_lambda_k  eigencount dichotomy for the cutoff       Section 3.3, Algorithm 1 step 1
- *   csc_filter           Jackson-damped Chebyshev filtering of the    Section 2.2 Step 1, Section 3.3,
- *                        new signals, eigencount check, refinement,   Eq. 6, Algorithm 1 steps 4-7
+ *   csc_estimate_lambda_k  eigencount dichotomy for the cutoff       Section 3.3, Algorithm 1
+ *   csc_filter           Jackson-damped Chebyshev filtering of the    Section 2.2, Section 3.3,
+ *                        new signals, eigencount check, refinement,   Eq. 6, Algorithm 1, Section 4.1
  *                        splice into the feature matrix Theta_t
- *   csc_cluster          row normalisation + k-means on Theta_t       Eq. 1, Eq. 5, Algorithm 1 step 8
+ *   csc_cluster          row normalisation + k-means on Theta_t       Eq. 1, Eq. 5, Algorithm 1
  *
  * plus stateless-per-call building blocks used by tests and benchmarks
  * (csc_signals, csc_cheb_filter, csc_kmeans) and host-only helpers that need
@@ -135,7 +135,7 @@ double csc_count_tolerance(int k, int c);
 csc_status csc_count_from_moments(int m, const double* mu, double lambda_c, int d, int c,
                                   double* count_out);
 
-/* Algorithm 1 step 7 / Section 4.1 dichotomy on the moment-based eigencount:
+/* Section 4.1 dichotomy of Algorithm 1 on the moment-based eigencount:
  * with lambda_prev < 0 bisect [0, 2]; else test lambda_prev, then grow a bracket
  * 0.01 * 2^i toward k until the count crosses k, then bisect.  Accept when
  * |count - k| <= tau; at most max_steps evaluations.  Outputs the cutoff, its
@@ -146,7 +146,7 @@ csc_status csc_lambda_search_moments(int m, const double* mu, int d, int c, int 
 
 /* ---------------------------------------------------------------- building blocks */
 
-/* Section 2.2 Step 1: the n x c block of i.i.d. N(0, 1/d) signals for global column
+/* Section 2.2 (approximate features): the n x c block of i.i.d. N(0, 1/d) signals for global column
  * ids col0 .. col0+c-1 (Philox-4x32-10 counter (row, column), key seed;
  * Box-Muller).  out: dtype CSC_F32 or CSC_BF16, leading dimension ld >= c,
  * caller-owned, host or device per `where`. */
@@ -163,7 +163,7 @@ csc_status csc_cheb_filter(csc_ctx* ctx, int m, double lambda_c, const void* R, 
                            int64_t ldr, int r_where, float* psi_out, int64_t ldp, int psi_where,
                            double* mu_out);
 
-/* Eq. 1-2 k-means (Lloyd) on caller features Y (n x d, dtype CSC_F32 or CSC_BF16,
+/* Eq. 1-2 k-means (Lloyd) on caller features Y (n x d, d <= 1024, dtype CSC_F32 or CSC_BF16,
  * leading dimension ldy, host or device per y_where), used as given (no row
  * normalisation).  Initial centroids: rows init_idx (host int64[k], distinct, in
  * [0, n)) or, when prev_assign (host or device per assign_where, int32[n]) is
@@ -182,14 +182,14 @@ csc_status csc_kmeans(csc_ctx* ctx, const void* Y, int y_dtype, int64_t n, int d
 
 /* ---------------------------------------------------------------- Algorithm 1 */
 
-/* Algorithm 1 step 1 (Section 3.3): cutoff lambda_c whose eigencount of the d
+/* Initial cutoff of Algorithm 1 (Section 3.3): cutoff lambda_c whose eigencount of the d
  * signals the next csc_filter will draw (seed, the next d global column ids) is
  * within tau of k, by one moment pass of order m and the dichotomy on [0, 2].
  * Stores the cutoff on the context.  Outputs may be NULL. */
 csc_status csc_estimate_lambda_k(csc_ctx* ctx, int k, int m, int d, uint64_t seed,
                                  double* lambda_out, double* count_out, int* evals_out);
 
-/* Algorithm 1 steps 4-7 and Eq. 6 on the current snapshot.  First snapshot (or
+/* One snapshot of Algorithm 1 up to the clustering (Eq. 6, Section 4.1).  First snapshot (or
  * p == 0): filter d new signals.  Later snapshots: keep dp = floor(p d) columns of
  * Theta_{t-1} (the ring slots filtered most recently) and filter dq = d - dp new
  * signals.  Cutoff: lambda_c >= 0 is used as given; lambda_c < 0 uses the
@@ -212,7 +212,7 @@ csc_status csc_get_features(csc_ctx* ctx, void* dst, int dtype, int64_t ld, int 
 /* Trace moments mu_0..mu_{2m} of the last filtering pass (host double[len], len <= 2m+1). */
 csc_status csc_get_moments(csc_ctx* ctx, double* mu_out, int len);
 
-/* Algorithm 1 steps 2 and 8: k-means on the row-normalised Theta_t.  The first
+/* The clustering of Algorithm 1: k-means on the row-normalised Theta_t.  The first
  * call on a context starts from Forgy rows init_idx (host int64[k]; NULL = draw
  * with the counter-based generator, key seed ^ (t * 0x9E3779B97F4A7C15)); later
  * calls warm-start from the previous assignment (an empty cluster takes row

@@ -14,7 +14,7 @@ Modules
 laplacian   normalized Laplacian and its shifted form L~ = L - I (Section 2.1)
 chebyshev   Jackson-damped Chebyshev low-pass: coefficients, three-term
             recursion, moments, eigencount and the lambda_k dichotomy
-            (Sections 2.2 and 3.3, Algorithm 1 steps 5-7)
+            (Sections 2.2, 3.3 and 4.1)
 philox      Philox-4x32-10 counter-based generator and Box-Muller normals
             (the random signal block R of Section 2.2)
 kmeans      Lloyd k-means, the paper's cost C_X (Eq. 1) and brute force

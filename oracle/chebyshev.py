@@ -2,7 +2,7 @@
 
 The paper replaces the ideal low-pass H_k = U diag(I_k, 0) U^T (Eq. 3) by a
 polynomial filter h(L) = U h(Lambda) U^T evaluated with Chebyshev polynomials
-in O(|E| d m) operations (Section 2.2, Step 1; Section 3.3).  It does not print
+in O(|E| d m) operations (Section 2.2, approximate features; Section 3.3).  It does not print
 the coefficients; the readings taken here are:
 
 * h approximates the step 1[lambda <= lambda_c] on [0, 2].  With x = lambda - 1
@@ -13,13 +13,13 @@ the coefficients; the readings taken here are:
   method), alpha = pi/(m+2):
   g_j = [(m+2-j) sin(alpha) cos(j alpha) + cos(alpha) sin(j alpha)] / ((m+2) sin(alpha)),
   and a_j = g_j c_j.  The Jackson kernel is positive, so h stays in [0, 1] and
-  is monotone in lambda and in the cutoff.
+  is monotone in the cutoff (in lambda up to the kernel's small edge ripple).
 * T_j(L~) R comes from the three-term recursion T_0 R = R, T_1 R = L~ R,
   T_{j+1} R = 2 L~ T_j R - T_{j-1} R.
 * Eigencount (the paper's Section 3.3 cites eigencount techniques without
   stating the estimator): count(lambda_c) = (d/c) ||h(L) R_c||_F^2 for a block
   of c signals of variance 1/d, an unbiased estimate of tr(h(L)^2).
-* Dichotomy (Algorithm 1 step 7 and Section 4.1): accept a cutoff when
+* Dichotomy (Algorithm 1 and Section 4.1): accept a cutoff when
   |count - k| <= tau with tau = max(0.5, 2 sqrt(2k/c)); with no previous cutoff
   bisect [0, 2]; with a previous cutoff test it first, then grow a bracket
   geometrically (0.01 * 2^i) in the direction of k until the count crosses k,

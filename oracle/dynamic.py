@@ -2,10 +2,10 @@
 
 Per snapshot G_t (fixed vertex set):
 
-1. t = 1 (Algorithm 1 steps 1-2): draw d signals, find the cutoff by the
+1. t = 1 (the static start of Algorithm 1): draw d signals, find the cutoff by the
    dichotomy on [0, 2] using the eigencount of the filtered block, filter,
    cluster.
-2. t >= 2 (steps 4-8): keep dp = floor(p d) previously filtered columns, draw
+2. t >= 2 (the loop of Algorithm 1): keep dp = floor(p d) previously filtered columns, draw
    dq = d - dp new signals, filter them with the previous cutoff, compute the
    eigencount on them, keep the cutoff if the count is within tau of k, else
    refine it by the dichotomy (starting from the previous cutoff); the block

@@ -1,4 +1,4 @@
-"""Counter-based random signals (Section 2.2, Step 1).  Test infrastructure only.
+"""Counter-based random signals (Section 2.2, approximate features).  Test infrastructure only.
 
 The paper draws R in R^{n x d} with centred i.i.d. Gaussian entries of
 variance 1/d.  The method's draws must be reproducible per column so that a

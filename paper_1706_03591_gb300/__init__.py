@@ -53,14 +53,15 @@ def _arr(x, kind: str):
         return None, _abi.CSC_HOST, _abi.CSC_F32, 0
     if _is_torch(x):
         import torch
-        if x.dim() == 2 and x.stride(1) != 1 or x.dim() == 1 and x.stride(0) != 1:
+        if x.numel() > 1 and (x.dim() == 2 and x.stride(1) != 1 or x.dim() == 1 and x.stride(0) != 1):
             raise ValueError(f"{kind}: innermost dimension must be contiguous")
         where = _abi.CSC_DEVICE if x.is_cuda else _abi.CSC_HOST
         code = _abi.CSC_BF16 if x.dtype == torch.bfloat16 else _abi.CSC_F32
         ld = x.stride(0) if x.dim() == 2 else 0
         return C.c_void_p(x.data_ptr()), where, code, ld
     a = np.asarray(x)
-    if a.ndim == 2 and a.strides[1] != a.itemsize or a.ndim == 1 and a.strides[0] != a.itemsize:
+    if a.size > 1 and (a.ndim == 2 and a.strides[1] != a.itemsize
+                       or a.ndim == 1 and a.strides[0] != a.itemsize):
         raise ValueError(f"{kind}: innermost dimension must be contiguous")
     ld = a.strides[0] // a.itemsize if a.ndim == 2 else 0
     return C.c_void_p(a.ctypes.data), _abi.CSC_HOST, _abi.CSC_F32, ld
@@ -189,7 +190,7 @@ def csc_estimate_lambda_k(h, k: int, m: int, d: int, seed: int):
 
 
 def csc_filter(h, m: int, d: int, p: float, seed: int, k: int = 0, lambda_c: float = -1.0):
-    """Algorithm 1 steps 4-7; returns (lambda_c, count, dichotomy evaluations, columns filtered)."""
+    """Algorithm 1 (reuse, new filtering, eigencount check, refinement); returns (lambda_c, count, dichotomy evaluations, columns filtered)."""
     lam, cnt, ev, cols = C.c_double(), C.c_double(), C.c_int(), C.c_int()
     _check(_lib().csc_filter(h, m, d, p, seed, k, lambda_c, C.byref(lam), C.byref(cnt), C.byref(ev),
                              C.byref(cols)), h, "csc_filter")
@@ -210,7 +211,7 @@ def csc_get_moments(h, length: int) -> np.ndarray:
 
 
 def csc_cluster(h, k: int, seed: int, init_idx, assign_out):
-    """Algorithm 1 step 8; writes assign_out and returns (cost C_Theta, Lloyd passes)."""
+    """Algorithm 1 (clustering of the combined features); writes assign_out and returns (cost C_Theta, Lloyd passes)."""
     idx = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int64)
     ap, aw, _, _ = _arr(assign_out, "assign_out")
     cost, iters = C.c_double(), C.c_int()

@@ -2,7 +2,7 @@
 //
 // Host-side logic of the method lives here: the Jackson-damped coefficients
 // (Section 3.3), the eigencount from trace moments, the dichotomy for the cutoff
-// (Algorithm 1 steps 1 and 7, Section 4.1), the feature ring of Eq. 6 and the
+// (Algorithm 1, Section 4.1), the feature ring of Eq. 6 and the
 // Lloyd driver.  Every device step runs in the kernels of the other translation units.
 #include <algorithm>
 #include <cmath>
@@ -124,7 +124,7 @@ double count_moments(int m, const double* mu, const double* a, int d, int c) {
 
 double tolerance(int k, int c) { return std::max(0.5, 2.0 * std::sqrt(2.0 * k / (double)c)); }
 
-// Dichotomy with the control flow of Algorithm 1 step 7 (see csc.h).
+// Dichotomy used by Algorithm 1 to refine the cutoff (Section 4.1; rule in csc.h).
 template <typename F>
 void search(F count, int k, double tau, double lam_prev, int max_steps, double* lam_out,
             double* cnt_out, int* evals_out) {
@@ -284,6 +284,10 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
     sa.col = csc::as<int32_t>(ctx->g.col);
     sa.val = ctx->g.weighted ? csc::as<float>(ctx->g.val) : nullptr;
     sa.scale = csc::as<float>(ctx->g.scale);
+    sa.vs = csc::as<float>(ctx->g.vs);
+    sa.ivs = csc::as<float>(ctx->g.ivs);
+    sa.blk_row = csc::as<int32_t>(ctx->g.blk_row);
+    sa.nblk = csc::edge_blocks(ctx->g.nnz);
     sa.psi = psi_dst ? psi_dst + c0 : nullptr;
     sa.ldp = ldp;
     sa.coef = csc::as<float>(ctx->coef);
@@ -301,6 +305,7 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
       sa.tn = csc::as<float>(ctx->tbuf[(j + 1) % 3]);
       sa.j = j;
       sa.part = tile_part + (size_t)(2 * (j + 1) - 1) * grid;
+      sa.tp_unscaled = j == 1;
       CUDA_OK(csc::launch_cheb_step(sa, j == 1 ? t0_dtype : CSC_F32, grid, s));
     }
     if (timed) CUDA_OK(cudaEventRecord(ctx->events[2 * tile + 1], s));
@@ -438,6 +443,7 @@ void csc_destroy(csc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   DevBuf* bufs[] = {&ctx->g.row_ptr, &ctx->g.col, &ctx->g.val, &ctx->g.scale, &ctx->g.deg,
+                    &ctx->g.blk_row, &ctx->g.vs, &ctx->g.ivs,
                     &ctx->tbuf[0], &ctx->tbuf[1], &ctx->tbuf[2], &ctx->psi, &ctx->part, &ctx->ef,
                     &ctx->coef, &ctx->rstage, &ctx->theta, &ctx->y, &ctx->slot_src,
                     &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad};
@@ -478,7 +484,10 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
   ALLOC_OK(csc::ensure(g.row_ptr, (size_t)(n + 1) * 8));
   ALLOC_OK(csc::ensure(g.col, (size_t)nnz * 4));
   ALLOC_OK(csc::ensure(g.scale, (size_t)n * 4));
+  ALLOC_OK(csc::ensure(g.vs, (size_t)n * 4));
+  ALLOC_OK(csc::ensure(g.ivs, (size_t)n * 4));
   ALLOC_OK(csc::ensure(g.deg, (size_t)n * 8));
+  ALLOC_OK(csc::ensure(g.blk_row, ((size_t)csc::edge_blocks(nnz) + 1) * 4));
   const cudaMemcpyKind kind = where == CSC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CUDA_OK(cudaMemcpyAsync(g.row_ptr.ptr, row_ptr, (size_t)(n + 1) * 8, kind, s));
   if (nnz > 0) CUDA_OK(cudaMemcpyAsync(g.col.ptr, col_idx, (size_t)nnz * 4, kind, s));
@@ -507,7 +516,8 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
     }
   }
   CUDA_OK(csc::launch_graph_prep(g, s));
-  ctx->launches += 1;
+  CUDA_OK(csc::launch_block_rows(g, s));
+  ctx->launches += 2;
   g.loaded = true;
   return CSC_OK;
 }
@@ -750,7 +760,7 @@ csc_status csc_kmeans(csc_ctx* ctx, const void* Y, int y_dtype, int64_t n, int d
                       int max_iter, int32_t* assign_out, int assign_where, double* centroids_out,
                       double* inertia_out, int* iters_out) {
   if (!ctx) return CSC_EINVAL;
-  if (!Y || n < 1 || d < 1 || ldy < d || k < 1 || k > n || !init_idx || !assign_out ||
+  if (!Y || n < 1 || d < 1 || d > 1024 || ldy < d || k < 1 || k > n || !init_idx || !assign_out ||
       !valid_dtype(y_dtype) || !valid_where(y_where) || !valid_where(assign_where))
     return fail(ctx, CSC_EINVAL, "csc_kmeans: bad arguments");
   for (int j = 0; j < k; ++j)

@@ -4,17 +4,26 @@
 //   Psi~ = sum_j a_j T_j R                                     (filter output)
 //   E_j = <T_j, T_j>,  F_j = <T_j, T_{j-1}>                     (float64 trace sums)
 //
+// Value-free form: the blocks are stored as V_j = S T_j (S = D^{-1/2}, 1 on isolated rows), so
+// V_{j+1} = -2 S^2 W V_j - V_{j-1}: a step gathers plain rows of V_j and needs only the edge
+// weights (none for unit weights), not D^{-1/2} of every neighbour.  Psi and the trace sums use
+// T = V / S.  The first step gathers T_0 = R with the weights w_e D^{-1/2}[col_e].
+//
 // so that mu_0 = E_0, mu_1 = F_1, mu_{2j} = 2 E_j - mu_0, mu_{2j-1} = 2 F_j - mu_1
 // (from T_i T_j = (T_{i+j} + T_{|i-j|}) / 2) give every moment mu_l = tr(R^T T_l R),
 // l <= 2m, and the eigencount of any cutoff without refiltering.
 //
 // One launch per step and column tile.  The tile is n x w float32 (w = 4 * LPR columns),
 // row-major with leading dimension w, so a gathered row is 4*w contiguous bytes.
-// A warp owns one row at a time; its 32 lanes form S = 32/LPR neighbour slots of LPR
-// lanes, each lane holding 4 consecutive columns (one 16-byte load per neighbour), so a
-// warp keeps S gathered rows in flight per iteration.  The S partial sums are folded with
-// xor shuffles; the slot-0 lanes run the epilogue (recursion, Psi update, dot products).
-// Rows are dealt round-robin to warps of a grid sized to fill every SM.
+// The rows are cut into blocks of about kEdgesPerBlock stored edges.  A CTA stages a
+// block's row offsets, column indices and edge weights w_e D^{-1/2}[col] in shared memory
+// with coalesced loads, so the gathers that follow depend on shared memory only.  A warp
+// then owns one row at a time: its 32 lanes form S = 32/LPR neighbour slots of LPR lanes,
+// each lane holding 4 consecutive columns (one 16-byte load per neighbour, four in
+// flight per lane), and the slot partials are folded with xor shuffles.  The own-row
+// operands (T_{j-1}, T_j, Psi) are loaded before the gather; the slot-0 lanes run the
+// epilogue (recursion, Psi update, dot products).  CTAs stride over the blocks of a grid
+// sized to fill every SM.
 #include "csc_internal.h"
 
 namespace csc {
@@ -51,29 +60,96 @@ __device__ __forceinline__ float4 shfl_xor4(float4 v, int off) {
   return v;
 }
 
-// sum_{p in row} w_p s_{col_p} T[col_p, 4 columns of this lane], folded over the S slots.
-template <int LPR, typename TG>
-__device__ __forceinline__ float4 gather_row(const StepArgs& a, const TG* __restrict__ tg,
-                                             int64_t row, int slot, int sub) {
-  constexpr int S = 32 / LPR;
-  const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
-  const int w = a.w;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  int64_t e = beg + slot;
-  for (; e + S < end; e += 2 * S) {
-    const int c0 = __ldg(a.col + e), c1 = __ldg(a.col + e + S);
-    float s0 = __ldg(a.scale + c0), s1 = __ldg(a.scale + c1);
-    if (a.val != nullptr) { s0 *= __ldg(a.val + e); s1 *= __ldg(a.val + e + S); }
-    const float4 v0 = ld4(tg + (int64_t)c0 * w + sub * 4);
-    const float4 v1 = ld4(tg + (int64_t)c1 * w + sub * 4);
-    fma4(acc, s0, v0);
-    fma4(acc, s1, v1);
+// Shared-memory staging of one edge block: row offsets (relative to the block's first edge),
+// column indices and per-edge weights.
+struct Stage {
+  int col[kEdgeBuf];
+  float wt[kEdgeBuf];
+  int rp[kRowBuf + 1];
+};
+
+constexpr int kStageUnroll = 4;
+
+// Loads block b into shared memory.  Edge weight: w_e (1 for unit weights), times
+// D^{-1/2}[col_e] when SCALED (first step, which gathers the unscaled T_0).  Returns false
+// (nothing staged) when the block's edge span or row count exceeds the buffers; the block is
+// then read directly from global memory.
+template <bool SCALED>
+__device__ __forceinline__ bool stage_block(const StepArgs& a, Stage& st, int b, int& rs, int& re) {
+  rs = __ldg(a.blk_row + b);
+  re = __ldg(a.blk_row + b + 1);
+  const int64_t es = __ldg(a.row_ptr + rs);
+  const int64_t ee = __ldg(a.row_ptr + re);
+  const bool fits = (ee - es) <= kEdgeBuf && (re - rs) <= kRowBuf;
+  if (!fits) return false;
+  for (int i = threadIdx.x; i <= re - rs; i += blockDim.x)
+    st.rp[i] = (int)(__ldcs(a.row_ptr + rs + i) - es);
+  const int ne = (int)(ee - es);
+  const bool need_w = SCALED || a.val != nullptr;
+  for (int base = 0; base < ne; base += kStageUnroll * blockDim.x) {
+    int c[kStageUnroll];
+    float v[kStageUnroll];
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int e = base + u * blockDim.x + threadIdx.x;
+      c[u] = e < ne ? __ldcs(a.col + es + e) : 0;
+      v[u] = (e < ne && a.val != nullptr) ? __ldcs(a.val + es + e) : 1.0f;
+    }
+    if (SCALED) {
+#pragma unroll
+      for (int u = 0; u < kStageUnroll; ++u)
+        if (base + u * blockDim.x + threadIdx.x < ne) v[u] *= __ldg(a.scale + c[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int e = base + u * blockDim.x + threadIdx.x;
+      if (e < ne) {
+        st.col[e] = c[u];
+        if (need_w) st.wt[e] = v[u];
+      }
+    }
   }
-  if (e < end) {
-    const int c0 = __ldg(a.col + e);
-    float s0 = __ldg(a.scale + c0);
-    if (a.val != nullptr) s0 *= __ldg(a.val + e);
-    fma4(acc, s0, ld4(tg + (int64_t)c0 * w + sub * 4));
+  return true;
+}
+
+constexpr int kGatherUnroll = 4;
+
+// sum_{e in row} wt_e X[col_e, 4 columns of this lane], folded over the S neighbour slots.
+// Staged: edges from shared memory, kGatherUnroll predicated loads in flight per lane.
+// Not staged: edges, weights (and D^{-1/2} when SCALED) from global memory.
+template <int LPR, bool SCALED, typename TG>
+__device__ __forceinline__ float4 gather_row(const StepArgs& a, const Stage& st, bool staged,
+                                             const TG* __restrict__ tg, int64_t row, int rl,
+                                             int slot, int sub) {
+  constexpr int S = 32 / LPR;
+  const int w = a.w;
+  const bool need_w = SCALED || a.val != nullptr;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const TG* base = tg + sub * 4;
+  if (staged) {
+    const int beg = st.rp[rl], end = st.rp[rl + 1];
+    for (int e0 = beg + slot; e0 < end; e0 += kGatherUnroll * S) {
+      float4 v[kGatherUnroll];
+      float wt[kGatherUnroll];
+#pragma unroll
+      for (int u = 0; u < kGatherUnroll; ++u) {
+        const int e = e0 + u * S;
+        const bool ok = e < end;
+        const int c = ok ? st.col[e] : 0;
+        wt[u] = ok ? (need_w ? st.wt[e] : 1.0f) : 0.0f;
+        v[u] = ok ? ld4(base + (int64_t)c * w) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kGatherUnroll; ++u) fma4(acc, wt[u], v[u]);
+    }
+  } else {
+    const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
+    for (int64_t e = beg + slot; e < end; e += S) {
+      const int c = __ldg(a.col + e);
+      float wv = a.val != nullptr ? __ldg(a.val + e) : 1.0f;
+      if (SCALED) wv *= __ldg(a.scale + c);
+      fma4(acc, wv, ld4(base + (int64_t)c * w));
+    }
   }
 #pragma unroll
   for (int off = LPR; off < 32; off <<= 1) acc = shfl_xor4(acc, off);
@@ -107,80 +183,166 @@ __device__ __forceinline__ void block_store(double (&acc)[NQ], double* part) {
 
 template <int LPR, typename T0>
 __global__ void __launch_bounds__(kBlock) cheb_first_kernel(StepArgs a) {
-  const int lane = threadIdx.x & 31;
+  __shared__ Stage st;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int slot = lane / LPR, sub = lane % LPR;
-  const int64_t warp = (blockIdx.x * (int64_t)kBlock + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
   const T0* __restrict__ t0 = static_cast<const T0*>(a.tg);
   const int w = a.w;
   float a0 = 0.f, a1 = 0.f;
   if (a.psi != nullptr) { a0 = __ldg(a.coef); a1 = __ldg(a.coef + 1); }
   double acc[3] = {0.0, 0.0, 0.0};  // <T0,T0>, <T1,T1>, <T1,T0>
-  for (int64_t row = warp; row < a.n; row += nwarps) {
-    const float4 g = gather_row<LPR, T0>(a, t0, row, slot, sub);
-    const float si = -__ldg(a.scale + row);
-    float e0 = 0.f, e1 = 0.f, f1 = 0.f;
-    if (slot == 0) {
-      const float4 t1 = make_float4(si * g.x, si * g.y, si * g.z, si * g.w);
-      const float4 own = ld4(t0 + row * w + sub * 4);
-      st4(a.tn + row * w + sub * 4, t1);
-      if (a.psi != nullptr) {
-        float4 p;
-        p.x = fmaf(a1, t1.x, a0 * own.x);
-        p.y = fmaf(a1, t1.y, a0 * own.y);
-        p.z = fmaf(a1, t1.z, a0 * own.z);
-        p.w = fmaf(a1, t1.w, a0 * own.w);
-        st4(a.psi + row * a.ldp + sub * 4, p);
+  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) {
+    int rs, re;
+    __syncthreads();
+    const bool staged = stage_block<true>(a, st, b, rs, re);
+    __syncthreads();
+    for (int r = rs + wid; r < re; r += kBlock / 32) {
+      const int64_t row = r;
+      float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (slot == 0) own = ld4(t0 + row * w + sub * 4);
+      const float si = -__ldg(a.scale + row);
+      const float vsi = __ldg(a.vs + row);
+      const float4 g = gather_row<LPR, true, T0>(a, st, staged, t0, row, r - rs, slot, sub);
+      float e0 = 0.f, e1 = 0.f, f1 = 0.f;
+      if (slot == 0) {
+        const float4 t1 = make_float4(si * g.x, si * g.y, si * g.z, si * g.w);
+        st4(a.tn + row * w + sub * 4, make_float4(vsi * t1.x, vsi * t1.y, vsi * t1.z, vsi * t1.w));
+        if (a.psi != nullptr) {
+          float4 p;
+          p.x = fmaf(a1, t1.x, a0 * own.x);
+          p.y = fmaf(a1, t1.y, a0 * own.y);
+          p.z = fmaf(a1, t1.z, a0 * own.z);
+          p.w = fmaf(a1, t1.w, a0 * own.w);
+          st4(a.psi + row * a.ldp + sub * 4, p);
+        }
+        e0 = dot4(own, own);
+        e1 = dot4(t1, t1);
+        f1 = dot4(t1, own);
       }
-      e0 = dot4(own, own);
-      e1 = dot4(t1, t1);
-      f1 = dot4(t1, own);
+      fold_dot<LPR>(e0, acc[0], lane);
+      fold_dot<LPR>(e1, acc[1], lane);
+      fold_dot<LPR>(f1, acc[2], lane);
     }
-    fold_dot<LPR>(e0, acc[0], lane);
-    fold_dot<LPR>(e1, acc[1], lane);
-    fold_dot<LPR>(f1, acc[2], lane);
   }
   block_store<3>(acc, a.part);
 }
 
+// Row-parallel variant of the gather for the general step: the LPR lanes of one slot own
+// one row; kRowUnroll predicated 16-byte loads per lane are in flight per batch.
+constexpr int kRowUnroll = 8;
+
+template <int LPR>
+__device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const Stage& st, bool staged,
+                                                 const float* __restrict__ tg, int64_t row, int rl,
+                                                 bool valid, int sub) {
+  const int w = a.w;
+  const float* base = tg + sub * 4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!valid) return acc;
+  if (staged) {
+    const int beg = st.rp[rl], end = st.rp[rl + 1];
+    const bool weighted = a.val != nullptr;
+    for (int e0 = beg; e0 < end; e0 += kRowUnroll) {
+      float4 v[kRowUnroll];
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        const int e = e0 + u;
+        v[u] = e < end ? ld4(base + (int64_t)st.col[e] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      if (weighted) {
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u)
+          if (e0 + u < end) fma4(acc, st.wt[e0 + u], v[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u) {
+          acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
+        }
+      }
+    }
+  } else {
+    const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
+    for (int64_t e = beg; e < end; ++e) {
+      const int c = __ldg(a.col + e);
+      const float wv = a.val != nullptr ? __ldg(a.val + e) : 1.0f;
+      fma4(acc, wv, ld4(base + (int64_t)c * w));
+    }
+  }
+  return acc;
+}
+
 template <int LPR, typename TP>
-__global__ void __launch_bounds__(kBlock) cheb_step_kernel(StepArgs a) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kBlock, 3) cheb_step_kernel(StepArgs a) {
+  __shared__ Stage st;
+  constexpr int S = 32 / LPR;
+  constexpr int kRowsPerPass = (kBlock / 32) * S;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int slot = lane / LPR, sub = lane % LPR;
-  const int64_t warp = (blockIdx.x * (int64_t)kBlock + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
   const float* __restrict__ tg = static_cast<const float*>(a.tg);
   const TP* __restrict__ tp = static_cast<const TP*>(a.tp);
   const int w = a.w;
   const float aj = a.psi != nullptr ? __ldg(a.coef + a.j + 1) : 0.f;
   double acc[2] = {0.0, 0.0};  // <T_{j+1},T_{j+1}>, <T_{j+1},T_j>
-  for (int64_t row = warp; row < a.n; row += nwarps) {
-    const float4 g = gather_row<LPR, float>(a, tg, row, slot, sub);
-    const float si2 = -2.0f * __ldg(a.scale + row);
-    float e = 0.f, f = 0.f;
-    if (slot == 0) {
-      const float4 prev = ld4(tp + row * w + sub * 4);
-      const float4 own = ld4(tg + row * w + sub * 4);
-      float4 t;
-      t.x = fmaf(si2, g.x, -prev.x);
-      t.y = fmaf(si2, g.y, -prev.y);
-      t.z = fmaf(si2, g.z, -prev.z);
-      t.w = fmaf(si2, g.w, -prev.w);
-      st4(a.tn + row * w + sub * 4, t);
-      if (a.psi != nullptr) {
-        float* pp = a.psi + row * a.ldp + sub * 4;
-        float4 p = ld4(pp);
-        p.x = fmaf(aj, t.x, p.x);
-        p.y = fmaf(aj, t.y, p.y);
-        p.z = fmaf(aj, t.z, p.z);
-        p.w = fmaf(aj, t.w, p.w);
-        st4(pp, p);
+  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) {
+    int rs, re;
+    __syncthreads();
+    const bool staged = stage_block<false>(a, st, b, rs, re);
+    __syncthreads();
+    for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
+      const int r = r0 + wid * S + slot;
+      const bool valid = r < re;
+      const int64_t row = valid ? r : rs;
+      // own-row operands are independent of the gather: issue them first
+      float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), own = prev, p = prev;
+      float vsi = 1.f, ivsi = 1.f;
+      if (valid) {
+        vsi = __ldg(a.vs + row);
+        ivsi = __ldg(a.ivs + row);
+        prev = ld4(tp + row * w + sub * 4);
+        own = ld4(tg + row * w + sub * 4);
+        if (a.psi != nullptr) p = ld4(a.psi + row * a.ldp + sub * 4);
       }
-      e = dot4(t, t);
-      f = dot4(t, own);
+      const float4 g = gather_own_row<LPR>(a, st, staged, tg, row, r - rs, valid, sub);
+      float e = 0.f, f = 0.f;
+      if (valid) {
+        // V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1};  T = V / vs
+        const float c2 = -2.0f * vsi * vsi;
+        if (a.tp_unscaled) { prev.x *= vsi; prev.y *= vsi; prev.z *= vsi; prev.w *= vsi; }
+        float4 v;
+        v.x = fmaf(c2, g.x, -prev.x);
+        v.y = fmaf(c2, g.y, -prev.y);
+        v.z = fmaf(c2, g.z, -prev.z);
+        v.w = fmaf(c2, g.w, -prev.w);
+        st4(a.tn + row * w + sub * 4, v);
+        const float4 t = make_float4(v.x * ivsi, v.y * ivsi, v.z * ivsi, v.w * ivsi);
+        const float4 tc = make_float4(own.x * ivsi, own.y * ivsi, own.z * ivsi, own.w * ivsi);
+        if (a.psi != nullptr) {
+          p.x = fmaf(aj, t.x, p.x);
+          p.y = fmaf(aj, t.y, p.y);
+          p.z = fmaf(aj, t.z, p.z);
+          p.w = fmaf(aj, t.w, p.w);
+          st4(a.psi + row * a.ldp + sub * 4, p);
+        }
+        e = dot4(t, t);
+        f = dot4(t, tc);
+      }
+      // fold over the LPR lanes of the slot; its first lane accumulates in float64
+#pragma unroll
+      for (int off = 1; off < LPR; off <<= 1) {
+        e += __shfl_xor_sync(kFull, e, off);
+        f += __shfl_xor_sync(kFull, f, off);
+      }
+      if (sub == 0 && valid) {
+        acc[0] += (double)e;
+        acc[1] += (double)f;
+      }
     }
-    fold_dot<LPR>(e, acc[0], lane);
-    fold_dot<LPR>(f, acc[1], lane);
+  }
+  // every lane may hold a partial: reduce the warp first
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc[0] += __shfl_xor_sync(kFull, acc[0], off);
+    acc[1] += __shfl_xor_sync(kFull, acc[1], off);
   }
   block_store<2>(acc, a.part);
 }

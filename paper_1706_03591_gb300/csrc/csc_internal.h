@@ -37,9 +37,20 @@ struct Graph {
   DevBuf col;       // int32[nnz]
   DevBuf val;       // float[nnz] (weighted only)
   DevBuf scale;     // float[n], D^{-1/2} (0 for isolated nodes)
+  DevBuf vs;        // float[n], row scale of the value-free recursion: D^{-1/2}, 1 if isolated
+  DevBuf ivs;       // float[n], 1 / vs
   DevBuf deg;       // double[n]
+  DevBuf blk_row;   // int32[nblk+1], edge-block partition of the rows for the recursion
   bool loaded = false;
 };
+
+// Target number of stored edges per block of the recursion kernels (staged in shared memory).
+constexpr int kEdgesPerBlock = 2048;
+// Shared-memory capacity of a staged block: a block whose edge span or row count exceeds
+// these is processed directly from global memory.
+constexpr int kEdgeBuf = 3072;
+constexpr int kRowBuf = 512;
+int edge_blocks(int64_t nnz);
 
 // ------------------------------------------------------------------ launch helpers
 
@@ -49,6 +60,8 @@ int grid_for(const void* kernel, int block, size_t smem = 0);
 // ------------------------------------------------------------------ graph kernels (graph.cu)
 
 cudaError_t launch_graph_prep(const Graph& g, cudaStream_t s);
+// Computes g.blk_row (edge_blocks(g.nnz) + 1 entries).
+cudaError_t launch_block_rows(const Graph& g, cudaStream_t s);
 // Device-side CSR validation; writes the number of violations into *bad (device int64).
 cudaError_t launch_graph_check(const Graph& g, unsigned long long* bad, cudaStream_t s);
 
@@ -70,7 +83,12 @@ struct StepArgs {
   const int64_t* row_ptr;
   const int32_t* col;
   const float* val;     // nullptr: unit weights
-  const float* scale;   // D^{-1/2}
+  const float* scale;   // D^{-1/2} (first step's per-edge weights)
+  const float* vs;      // row scale of the stored blocks V_j = vs * T_j (j >= 1)
+  const float* ivs;     // 1 / vs
+  const int32_t* blk_row;  // edge-block partition (nblk + 1)
+  int nblk;
+  int tp_unscaled;      // 1: tp holds T_{j-1} (step 2 reads T_0 = R), 0: tp holds V_{j-1}
   const void* tg;       // gathered block T_j (n x w)
   const void* tp;       // T_{j-1} (own rows), unused on the first step
   float* tn;            // T_{j+1} (n x w)
@@ -82,10 +100,12 @@ struct StepArgs {
   int w;                // tile width (= 4 * lanes per row)
 };
 
-// First step: T_1 = L~ T_0, Psi = a_0 T_0 + a_1 T_1, partials {<T0,T0>, <T1,T1>, <T1,T0>}.
+// First step: T_1 = L~ T_0 (stored as V_1 = vs T_1), Psi = a_0 T_0 + a_1 T_1,
+// partials {<T0,T0>, <T1,T1>, <T1,T0>}.
 cudaError_t launch_cheb_first(const StepArgs& a, int t0_dtype, int grid, cudaStream_t s);
-// General step: T_{j+1} = 2 L~ T_j - T_{j-1}, Psi += a_{j+1} T_{j+1}, partials
-// {<T_{j+1},T_{j+1}>, <T_{j+1},T_j>}.  tp_dtype is the storage type of T_{j-1}.
+// General step on the stored blocks V_j = vs T_j:
+// V_{j+1} = -2 vs_i^2 sum_e w_e V_j[col_e] - V_{j-1}, Psi += a_{j+1} T_{j+1}, partials
+// {<T_{j+1},T_{j+1}>, <T_{j+1},T_j>}.  tp_dtype is the storage type of tp.
 cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStream_t s);
 int cheb_grid(int w);
 // Sums partials[(q * nslots + slot) * grid + b] over b (fixed order) into out[q * nslots + slot]
@@ -107,18 +127,24 @@ cudaError_t launch_convert(const void* src, int src_dtype, int64_t ld_src, void*
 // ------------------------------------------------------------------ k-means (kmeans.cu)
 
 struct KmeansState {
-  DevBuf c64, c32, cn2, cmax;   // centroids float64 [k][dp], float32 [kp][dp], |c|^2 [kp], max|c|
-  DevBuf sums, counts;          // int64 [k][dp], int32 [k]
-  DevBuf assign_a, assign_b;    // int32 [n]
-  DevBuf flagged, counters;     // int32 [n]; unsigned long long [4]
-  DevBuf maxabs;                // float bits (uint32)
-  DevBuf inertia_part;          // double [grid]
+  DevBuf c64, c32, cn2;         // centroids float64 [k][d], float32 [k][d], |c32|^2 [k]
+  DevBuf cmove;                 // float [k], movement of each centroid in the last update
+  DevBuf bits;                  // uint32 [4]: max |c| and max movement (float bits), max |y|
+  DevBuf sums, counts;          // fixed-point int64 [k][d], int32 [k]
+  DevBuf assign;                // int32 [n]
+  DevBuf ub, lbk;               // float [n], [n][k]: distance bounds (pruning)
+  DevBuf vstamp;                // int32 [n]: centroid version the bounds of a row refer to
+  DevBuf drift;                 // float [passes][k]: movement bound since each version
+  DevBuf work, flagged, moved;  // int32 [n], [n], [3][n]
+  DevBuf counters;              // unsigned long long [4]: moved, flagged, work
+  DevBuf inertia_part;          // double [grid + 1]
   DevBuf init_idx;              // int64 [k]
 };
 
 struct KmeansResult {
   int iters = 0;
   bool converged = false;
+  int64_t decided = 0;         // rows decided by the distance pass over all passes (pruning stats)
   double inertia = 0.0;
   int32_t* assign = nullptr;   // device pointer to the final assignment (inside the state)
   int64_t launches = 0;        // kernels launched

@@ -1,4 +1,10 @@
-// k-means (Lloyd) on the feature rows (Section 2.1, Eq. 1-2; Algorithm 1 step 8).
+// k-means (Lloyd) on the feature rows (Section 2.1, Eq. 1-2; the clustering of Algorithm 1).
+//
+// Pruning (Elkan's bounds): each row keeps an upper bound on its distance to its centroid and
+// a lower bound on its distance to each centroid.  After an update moves centroid j by
+// delta_j, the bounds become ub + delta_a and lb_j - delta_j (rounded outward); only the
+// centroids whose lower bound falls below ub are re-measured, and a row with none keeps its
+// centroid without reading its features.  The decisions are the same as without pruning.
 //
 // Assignment: a register-tiled float32 pass computes f_j = |c_j|^2 - 2 <y, c_j> for every
 // centroid and keeps, per row, the best and second-best value.  |f_j - e_j| (e_j the exact
@@ -12,9 +18,13 @@
 // Update: centroid sums are accumulated exactly in 64-bit fixed point (y * 2^S rounded to
 // an integer, S chosen so that n max|y| 2^S < 2^62), privatised per block in shared memory
 // when k*d fits, then converted to float64 means.  Integer addition is associative, so the
-// result does not depend on scheduling; an empty cluster keeps its centroid.
+// result does not depend on scheduling; an empty cluster keeps its centroid.  After the first
+// pass only the rows that changed cluster add and subtract their quantised features, which
+// gives exactly the same sums.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "csc_internal.h"
@@ -88,29 +98,39 @@ __global__ void update_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, 
   }
 }
 
-// Means from the fixed-point sums (empty clusters keep c64), float32 copies, |c32|^2, max |c|.
+// Means from the fixed-point sums (an empty cluster keeps its centroid), the float32 copies,
+// |c32|^2, and for the pruning bounds the movement of every centroid (rounded up) and the
+// largest movement.  One warp per centroid.
 __global__ void finalize_kernel(const unsigned long long* __restrict__ sums,
                                 const int* __restrict__ counts, int k, int d, double inv_scale,
                                 double* __restrict__ c64, float* __restrict__ c32,
-                                float* __restrict__ cn2, unsigned int* __restrict__ cmax_bits) {
-  for (int e = threadIdx.x; e < k * d; e += blockDim.x) {
-    const int j = e / d;
-    const int cnt = counts[j];
-    if (cnt > 0) c64[e] = (double)(long long)sums[e] * inv_scale / (double)cnt;
-    c32[e] = (float)c64[e];
-  }
-  __syncthreads();
+                                float* __restrict__ cn2, float* __restrict__ cmove,
+                                unsigned int* __restrict__ cmax_bits,
+                                unsigned int* __restrict__ dmax_bits) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < k; j += nw) {
-    double s = 0.0;
+    const int cnt = counts[j];
+    double mv = 0.0, nrm = 0.0;
     for (int l = lane; l < d; l += 32) {
-      const double v = (double)c32[(size_t)j * d + l];
-      s += v * v;
+      const size_t e = (size_t)j * d + l;
+      const double old = c64[e];
+      const double nwv = cnt > 0 ? (double)(long long)sums[e] * inv_scale / (double)cnt : old;
+      mv += (nwv - old) * (nwv - old);
+      c64[e] = nwv;
+      const float f = (float)nwv;
+      c32[e] = f;
+      nrm += (double)f * (double)f;
     }
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    for (int off = 16; off > 0; off >>= 1) {
+      mv += __shfl_xor_sync(0xffffffffu, mv, off);
+      nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+    }
     if (lane == 0) {
-      cn2[j] = (float)s;
-      atomicMax(cmax_bits, __float_as_uint((float)sqrt(s) * 1.0000002f));
+      cn2[j] = (float)nrm;
+      const float move = __double2float_ru(sqrt(mv) * (1.0 + 1e-12));
+      cmove[j] = move;
+      atomicMax(cmax_bits, __float_as_uint(__double2float_ru(sqrt(nrm) * (1.0 + 1e-7))));
+      atomicMax(dmax_bits, __float_as_uint(move));
     }
   }
 }
@@ -122,10 +142,14 @@ struct AssignArgs {
   const float* c32;   // [k][d]
   const float* cn2;   // [k]
   const unsigned int* cmax_bits;
-  const int32_t* old_assign;  // nullptr on the first pass
-  int32_t* new_assign;
+  const int32_t* work;           // rows to decide (nullptr: all rows)
+  int32_t* assign;               // in/out
+  float* ub;                     // upper bound on the distance to the assigned centroid
+  float* lbk;                    // [n][k] lower bounds on the distance to every centroid
   int32_t* flagged;
-  unsigned long long* counters;  // [0] changed rows, [1] flagged rows
+  int32_t* moved;                // [3][n]: row, old, new
+  unsigned long long* counters;  // [0] moved, [1] flagged, [2] work
+  int track;                     // append changed rows to `moved`
 };
 
 __device__ __forceinline__ void merge_best(float& b, int& bi, float& s, float b2, int bi2, float s2) {
@@ -138,21 +162,31 @@ __device__ __forceinline__ void merge_best(float& b, int& bi, float& s, float b2
   }
 }
 
+__device__ __forceinline__ void record_move(const AssignArgs& a, int64_t row, int old, int nw) {
+  const unsigned long long m = atomicAdd(a.counters, 1ull);
+  a.moved[m] = (int32_t)row;
+  a.moved[a.n + m] = old;
+  a.moved[2 * a.n + m] = nw;
+}
+
 template <typename TY>
 __global__ void __launch_bounds__(kAssignBlock) assign_kernel(AssignArgs a) {
   __shared__ __align__(16) float Ys[BK][BM + 4];
   __shared__ __align__(16) float Cs[BK][BN + 4];
-  __shared__ unsigned long long block_changed;
+  __shared__ int64_t rows_s[BM];
   const TY* __restrict__ y = static_cast<const TY*>(a.y);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const float cmax = __uint_as_float(*a.cmax_bits);
-  const float u = 5.9604644775390625e-8f;
-  const int64_t ntiles = (a.n + BM - 1) / BM;
-  if (tid == 0) block_changed = 0;
-  __syncthreads();
-  unsigned long long changed = 0;
+  const double u = 5.9604644775390625e-8;
+  const int64_t count = a.work != nullptr ? (int64_t)a.counters[2] : a.n;
+  const int64_t ntiles = (count + BM - 1) / BM;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t row0 = tile * BM;
+    __syncthreads();
+    if (tid < BM) {
+      const int64_t t = tile * BM + tid;
+      rows_s[tid] = t < count ? (a.work != nullptr ? (int64_t)a.work[t] : t) : -1;
+    }
+    __syncthreads();
     float best[4], second[4], yn2[4];
     int bidx[4];
 #pragma unroll
@@ -166,9 +200,9 @@ __global__ void __launch_bounds__(kAssignBlock) assign_kernel(AssignArgs a) {
       for (int k0 = 0; k0 < a.d; k0 += BK) {
         for (int e = tid; e < BM * BK; e += kAssignBlock) {
           const int r = e / BK, kk = e % BK;
-          const int64_t row = row0 + r;
+          const int64_t row = rows_s[r];
           const int col = k0 + kk;
-          Ys[kk][r] = (row < a.n && col < a.d) ? ldf(y + row * a.ldy + col) : 0.f;
+          Ys[kk][r] = (row >= 0 && col < a.d) ? ldf(y + row * a.ldy + col) : 0.f;
         }
         for (int e = tid; e < BN * BK; e += kAssignBlock) {
           const int jj = e / BK, kk = e % BK;
@@ -201,6 +235,15 @@ __global__ void __launch_bounds__(kAssignBlock) assign_kernel(AssignArgs a) {
             const float f = fmaf(-2.0f, acc[i][j], c2);
             if (f < best[i]) { second[i] = best[i]; best[i] = f; bidx[i] = cj; }
             else if (f < second[i]) second[i] = f;
+            const int64_t row = rows_s[ty * 4 + i];
+            if (row >= 0) {
+              // lower bound on |y - c_j| from f_j and its error bound (squared distance = |y|^2 + f)
+              const double yn = (double)yn2[i];
+              const double slack = u * (3.1 * cmax * cmax + 2.0 * (1.01 * a.d + 1.0) * sqrt(yn) * cmax) +
+                                   2.0 * (a.d + 2.0) * u * yn;
+              const double dl = (double)f + yn - slack;
+              a.lbk[row * a.k + cj] = dl > 0.0 ? __double2float_rd(sqrt(dl) * (1.0 - 1e-6)) : 0.0f;
+            }
           }
         }
       }
@@ -219,52 +262,227 @@ __global__ void __launch_bounds__(kAssignBlock) assign_kernel(AssignArgs a) {
     if (tx == 0) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int64_t row = row0 + ty * 4 + i;
-        if (row >= a.n) continue;
-        const float bound = u * (3.1f * cmax * cmax + 2.0f * (1.01f * a.d + 1.0f) * sqrtf(yn2[i]) * cmax);
-        const bool tie = !(second[i] - best[i] > 4.0f * bound);
-        if (tie) {
+        const int64_t row = rows_s[ty * 4 + i];
+        if (row < 0) continue;
+        const double yn = (double)yn2[i];
+        const double bound = u * (3.1 * cmax * cmax + 2.0 * (1.01 * a.d + 1.0) * sqrt(yn) * cmax);
+        if (!((double)second[i] - (double)best[i] > 4.0 * bound)) {
           const unsigned long long slot = atomicAdd(a.counters + 1, 1ull);
           a.flagged[slot] = (int32_t)row;
-        } else {
-          a.new_assign[row] = bidx[i];
-          if (a.old_assign != nullptr && a.old_assign[row] != bidx[i]) ++changed;
+          continue;
         }
+        // squared distance = yn2 + f, each known to within its error bound
+        const double slack = bound + 2.0 * (a.d + 2.0) * u * yn;
+        const double dmin = (double)best[i] + yn + slack;
+        a.ub[row] = __double2float_ru(sqrt(fmax(dmin, 0.0)) * (1.0 + 1e-6));
+        const int old = a.assign[row];
+        a.assign[row] = bidx[i];
+        if (a.track && old != bidx[i]) record_move(a, row, old, bidx[i]);
       }
     }
   }
-  if (changed) atomicAdd(&block_changed, changed);
-  __syncthreads();
-  if (tid == 0 && block_changed) atomicAdd(a.counters, block_changed);
 }
 
 // Float64 decision for the flagged rows: one warp per row, all centroids, lowest index on ties.
 template <typename TY>
-__global__ void recheck_kernel(const TY* __restrict__ y, int64_t ldy, int d, int k,
-                               const double* __restrict__ c64, const int32_t* __restrict__ flagged,
-                               const unsigned long long* __restrict__ counters,
-                               const int32_t* __restrict__ old_assign, int32_t* __restrict__ new_assign,
-                               unsigned long long* changed) {
-  const unsigned long long nflag = counters[1];
+__global__ void recheck_kernel(AssignArgs a, const double* __restrict__ c64) {
+  const TY* __restrict__ y = static_cast<const TY*>(a.y);
+  const unsigned long long nflag = a.counters[1];
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = warp; w < (int64_t)nflag; w += nwarps) {
-    const int64_t row = flagged[w];
-    double best = INFINITY;
+    const int64_t row = a.flagged[w];
+    double best = INFINITY, second = INFINITY;
     int bi = 0;
-    for (int j = 0; j < k; ++j) {
+    for (int j = 0; j < a.k; ++j) {
       double s = 0.0;
-      for (int l = lane; l < d; l += 32) {
-        const double diff = (double)ldf(y + row * ldy + l) - c64[(size_t)j * d + l];
+      for (int l = lane; l < a.d; l += 32) {
+        const double diff = (double)ldf(y + row * a.ldy + l) - c64[(size_t)j * a.d + l];
         s = fma(diff, diff, s);
       }
       for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (s < best) { best = s; bi = j; }
+      if (lane == 0) a.lbk[row * a.k + j] = __double2float_rd(sqrt(s) * (1.0 - 1e-9));
+      if (s < best) { second = best; best = s; bi = j; }
+      else if (s < second) second = s;
     }
     if (lane == 0) {
-      new_assign[row] = bi;
-      if (old_assign != nullptr && old_assign[row] != bi) atomicAdd(changed, 1ull);
+      a.ub[row] = __double2float_ru(sqrt(best) * (1.0 + 1e-9));
+      const int old = a.assign[row];
+      a.assign[row] = bi;
+      if (a.track && old != bi) record_move(a, row, old, bi);
+    }
+  }
+}
+
+// Pruned Lloyd pass (Elkan's bounds), lazily updated.  A row's bounds refer to the centroid
+// version vstamp[row] at which they were last written; drift[v][j] (rounded up) bounds how far
+// centroid j moved since version v, so the current bounds are ub + drift[v][a] and
+// lb_j - drift[v][j].  Rows whose bounds still exclude every other centroid are neither read
+// again nor rewritten.
+
+// Scan: marks the rows with at least one candidate centroid (lb_j <= ub, j != a).
+__global__ void elkan_scan_kernel(int64_t n, int k, const int32_t* __restrict__ assign,
+                                  const int32_t* __restrict__ vstamp, const float* __restrict__ ub,
+                                  const float* __restrict__ lbk, const float* __restrict__ drift,
+                                  int32_t* __restrict__ work, unsigned long long* __restrict__ counters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = warp; row < n; row += nwarps) {
+    const int asg = __ldg(assign + row);
+    const float* dv = drift + (size_t)__ldg(vstamp + row) * k;
+    const float u = __fadd_ru(__ldg(ub + row), __ldg(dv + asg));
+    const float* lrow = lbk + row * k;
+    bool cand = false;
+    for (int j = lane; j < k; j += 32)
+      cand |= (j != asg) && !(u < __fsub_rd(__ldcs(lrow + j), __ldg(dv + j)));
+    if (__any_sync(0xffffffffu, cand) && lane == 0) {
+      const unsigned long long slot = atomicAdd(counters + 2, 1ull);
+      work[slot] = (int32_t)row;
+    }
+  }
+}
+
+// Refine: one warp per listed row.  Brings the bounds to the current version, measures the
+// distance to the own centroid (tightening ub) and to every remaining candidate in float32
+// with its error bound e(D) = (d+3) u D + 2u sqrt(D) cmax, and decides.  When the best two are
+// closer than their error bounds, the candidates that can still be the minimum are measured
+// in float64 (lowest index on ties); the other centroids are provably farther.
+template <typename TY, int DW>
+__global__ void elkan_refine_kernel(AssignArgs a, const int32_t* __restrict__ work,
+                                    const float* __restrict__ drift, int32_t* __restrict__ vstamp,
+                                    int version, const double* __restrict__ c64) {
+  const TY* __restrict__ y = static_cast<const TY*>(a.y);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float cmax = __uint_as_float(*a.cmax_bits);
+  const float u = 5.9604644775390625e-8f;
+  const int d = a.d, k = a.k;
+  const float erel = (d + 3.0f) * u;
+  const float eabs = 2.0f * u * cmax;
+  const int64_t nwork = (int64_t)a.counters[2];
+  for (int64_t w = warp; w < nwork; w += nwarps) {
+    const int64_t row = work[w];
+    const int asg = a.assign[row];
+    const float* dv = drift + (size_t)vstamp[row] * k;
+    float* lrow = a.lbk + row * k;
+    for (int j = lane; j < k; j += 32) lrow[j] = fmaxf(__fsub_rd(lrow[j], __ldg(dv + j)), 0.0f);
+    float yv[DW];
+#pragma unroll
+    for (int i = 0; i < DW; ++i) {
+      const int l = lane + 32 * i;
+      yv[i] = l < d ? ldf(y + row * a.ldy + l) : 0.0f;
+    }
+    __syncwarp();
+    auto dist = [&](int j) {
+      const float* c = a.c32 + (size_t)j * d;
+      float sacc = 0.f;
+#pragma unroll
+      for (int i = 0; i < DW; ++i) {
+        const int l = lane + 32 * i;
+        if (l < d) {
+          const float df = yv[i] - __ldg(c + l);
+          sacc = fmaf(df, df, sacc);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+      return sacc;
+    };
+    auto dist64 = [&](int j) {
+      const double* c = c64 + (size_t)j * d;
+      double sacc = 0.0;
+#pragma unroll
+      for (int i = 0; i < DW; ++i) {
+        const int l = lane + 32 * i;
+        if (l < d) {
+          const double df = (double)yv[i] - c[l];
+          sacc = fma(df, df, sacc);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+      return sacc;
+    };
+    const float da = dist(asg), ea = erel * da + eabs * sqrtf(da);
+    const float ub = __fsqrt_ru(__fadd_ru(da, ea));
+    float best = da, ebest = ea;
+    int bi = asg;
+    float second = INFINITY, esecond = 0.f;
+    for (int j0 = 0; j0 < k; j0 += 32) {
+      const int j = j0 + lane;
+      const bool cand = j < k && j != asg && !(ub < lrow[j]);
+      unsigned mask = __ballot_sync(0xffffffffu, cand);
+      while (mask) {
+        const int q = j0 + __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float dq = dist(q), eq = erel * dq + eabs * sqrtf(dq);
+        if (lane == (q & 31)) lrow[q] = __fsqrt_rd(fmaxf(__fsub_rd(dq, eq), 0.0f));
+        if (dq < best || (dq == best && q < bi)) {
+          second = best; esecond = ebest;
+          best = dq; ebest = eq; bi = q;
+        } else if (dq < second) {
+          second = dq; esecond = eq;
+        }
+      }
+    }
+    if (!(second - best > ebest + esecond)) {
+      // near tie: float64 on every centroid whose lower bound still admits the minimum
+      // (true distance^2 <= best + ebest); the others are provably farther
+      __syncwarp();
+      const float limit = __fsqrt_ru(__fadd_ru(best, 2.0f * ebest));
+      double b64 = dist64(asg);
+      int b64i = asg;
+      for (int j0 = 0; j0 < k; j0 += 32) {
+        const int j = j0 + lane;
+        const bool maybe = j < k && j != asg && lrow[j] <= limit;
+        unsigned mask = __ballot_sync(0xffffffffu, maybe);
+        while (mask) {
+          const int q = j0 + __ffs(mask) - 1;
+          mask &= mask - 1;
+          const double dq = dist64(q);
+          if (dq < b64 || (dq == b64 && q < b64i)) { b64 = dq; b64i = q; }
+        }
+      }
+      bi = b64i;
+      best = (float)b64;
+      ebest = __fmul_ru((float)b64, 1e-6f) + eabs;
+    }
+    if (lane == 0) {
+      a.ub[row] = __fsqrt_ru(__fadd_ru(best, ebest));
+      vstamp[row] = version;
+      if (bi != asg) {
+        lrow[asg] = __fsqrt_rd(fmaxf(__fsub_rd(da, ea), 0.0f));
+        a.assign[row] = bi;
+        if (a.track) record_move(a, row, asg, bi);
+      }
+    }
+  }
+}
+
+// Applies the fixed-point deltas of the rows that changed cluster: one warp per row.
+template <typename TY>
+__global__ void move_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d,
+                            const int32_t* __restrict__ moved, const unsigned long long* counters,
+                            float scale, unsigned long long* __restrict__ sums,
+                            int* __restrict__ counts) {
+  const unsigned long long nm = counters[0];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t m = warp; m < (int64_t)nm; m += nwarps) {
+    const int64_t row = moved[m];
+    const int old = moved[n + m], nw = moved[2 * n + m];
+    for (int l = lane; l < d; l += 32) {
+      const long long q = __float2ll_rn(ldf(y + row * ldy + l) * scale);
+      atomicAdd(sums + (size_t)nw * d + l, (unsigned long long)q);
+      atomicAdd(sums + (size_t)old * d + l, (unsigned long long)(-q));
+    }
+    if (lane == 0) {
+      atomicAdd(counts + nw, 1);
+      atomicAdd(counts + old, -1);
     }
   }
 }
@@ -297,8 +515,17 @@ __global__ void inertia_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n,
   }
 }
 
+bool debug_on() {
+  static int on = -1;
+  if (on < 0) on = getenv("CSC_DEBUG") != nullptr;
+  return on == 1;
+}
+#define TRACE(msg) \
+  do { if (debug_on()) { fprintf(stderr, "[csc] %s\n", msg); fflush(stderr); } } while (0)
+
 #define CK(call)                                          \
   do {                                                    \
+    TRACE(#call);                                         \
     cudaError_t e_ = (call);                              \
     if (e_ != cudaSuccess) {                              \
       if (err) *err = std::string(#call ": ") + cudaGetErrorString(e_); \
@@ -307,27 +534,50 @@ __global__ void inertia_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n,
   } while (0)
 
 template <typename TY>
+cudaError_t launch_refine(int d, int sms, cudaStream_t s, const AssignArgs& aa, const int32_t* work,
+                          const float* drift, int32_t* vstamp, int version, const double* c64) {
+  const int grid = sms * 8, block = 256;
+  if (d <= 64)
+    elkan_refine_kernel<TY, 2><<<grid, block, 0, s>>>(aa, work, drift, vstamp, version, c64);
+  else if (d <= 128)
+    elkan_refine_kernel<TY, 4><<<grid, block, 0, s>>>(aa, work, drift, vstamp, version, c64);
+  else if (d <= 256)
+    elkan_refine_kernel<TY, 8><<<grid, block, 0, s>>>(aa, work, drift, vstamp, version, c64);
+  else if (d <= 512)
+    elkan_refine_kernel<TY, 16><<<grid, block, 0, s>>>(aa, work, drift, vstamp, version, c64);
+  else
+    elkan_refine_kernel<TY, 32><<<grid, block, 0, s>>>(aa, work, drift, vstamp, version, c64);
+  return cudaGetLastError();
+}
+
+template <typename TY>
 csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy, int k,
                      const int64_t* init_idx, const int32_t* prev_assign, int max_iter,
                      cudaStream_t s, KmeansResult* res, std::string* err) {
   const size_t kd = (size_t)k * d;
+  const int sms = num_sms();
   if (!ensure(st.c64, kd * 8) || !ensure(st.c32, kd * 4) || !ensure(st.cn2, (size_t)k * 4) ||
-      !ensure(st.cmax, 16) || !ensure(st.sums, kd * 8) || !ensure(st.counts, (size_t)k * 4) ||
-      !ensure(st.assign_a, (size_t)n * 4) || !ensure(st.assign_b, (size_t)n * 4) ||
-      !ensure(st.flagged, (size_t)n * 4) || !ensure(st.counters, 64) || !ensure(st.maxabs, 16) ||
-      !ensure(st.init_idx, (size_t)k * 8) || !ensure(st.inertia_part, (size_t)num_sms() * 8 * 8)) {
+      !ensure(st.cmove, (size_t)k * 4) || !ensure(st.bits, 16) || !ensure(st.sums, kd * 8) ||
+      !ensure(st.counts, (size_t)k * 4) || !ensure(st.assign, (size_t)n * 4) ||
+      !ensure(st.ub, (size_t)n * 4) || !ensure(st.lbk, (size_t)n * k * 4) ||
+      !ensure(st.work, (size_t)n * 4) || !ensure(st.flagged, (size_t)n * 4) ||
+      !ensure(st.moved, (size_t)n * 12) || !ensure(st.counters, 64) ||
+      !ensure(st.init_idx, (size_t)k * 8) || !ensure(st.inertia_part, ((size_t)sms * 8 + 1) * 8) ||
+      !ensure(st.vstamp, (size_t)n * 4) || !ensure(st.drift, (size_t)(max_iter + 1) * k * 4)) {
     if (err) *err = "k-means: device allocation failed";
     return CSC_ENOMEM;
   }
-  const int sms = num_sms();
+  unsigned int* bits = as<unsigned int>(st.bits);  // [0] max|c|, [1] max move, [2] max|y|
+  unsigned long long* counters = as<unsigned long long>(st.counters);
   int64_t launches = 0;
   // fixed-point scale from max |y|
-  CK(cudaMemsetAsync(st.maxabs.ptr, 0, 4, s));
-  maxabs_kernel<TY><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, as<unsigned int>(st.maxabs));
+  CK(cudaMemsetAsync(st.bits.ptr, 0, 16, s));
+  TRACE("maxabs");
+  maxabs_kernel<TY><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, bits + 2);
   CK(cudaGetLastError());
   ++launches;
   unsigned int mbits = 0;
-  CK(cudaMemcpyAsync(&mbits, st.maxabs.ptr, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&mbits, bits + 2, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   float maxabs;
   std::memcpy(&maxabs, &mbits, 4);
@@ -343,6 +593,7 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
 
   // initial centroids
   CK(cudaMemcpyAsync(st.init_idx.ptr, init_idx, (size_t)k * 8, cudaMemcpyHostToDevice, s));
+  TRACE("forgy");
   forgy_kernel<TY><<<std::max(1, (int)std::min<size_t>((kd + 255) / 256, 1024)), 256, 0, s>>>(
       y, ldy, as<int64_t>(st.init_idx), k, d, as<double>(st.c64));
   CK(cudaGetLastError());
@@ -357,11 +608,12 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     if (asg == nullptr) return cudaSuccess;
     ++launches;
     if (use_smem) {
-      auto fn = update_kernel<TY, true>;
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(update_kernel<TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
       if (e != cudaSuccess) return e;
-      fn<<<sms, 1024, smem, s>>>(y, ldy, n, d, asg, k, scale, as<unsigned long long>(st.sums),
-                                 as<int>(st.counts));
+      update_kernel<TY, true><<<sms, 1024, smem, s>>>(y, ldy, n, d, asg, k, scale,
+                                                      as<unsigned long long>(st.sums),
+                                                      as<int>(st.counts));
     } else {
       update_kernel<TY, false><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, asg, k, scale,
                                                        as<unsigned long long>(st.sums),
@@ -370,53 +622,100 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     return cudaGetLastError();
   };
   auto finalize = [&]() -> cudaError_t {
-    cudaError_t e = cudaMemsetAsync(st.cmax.ptr, 0, 4, s);
+    cudaError_t e = cudaMemsetAsync(st.bits.ptr, 0, 8, s);
     if (e != cudaSuccess) return e;
     ++launches;
     finalize_kernel<<<1, 1024, 0, s>>>(as<unsigned long long>(st.sums), as<int>(st.counts), k, d,
                                        inv_scale, as<double>(st.c64), as<float>(st.c32),
-                                       as<float>(st.cn2), as<unsigned int>(st.cmax));
+                                       as<float>(st.cn2), as<float>(st.cmove), bits, bits + 1);
     return cudaGetLastError();
   };
   CK(accumulate(prev_assign));
   CK(finalize());
 
-  int32_t* cur = as<int32_t>(st.assign_a);
-  int32_t* other = as<int32_t>(st.assign_b);
-  const int32_t* old = nullptr;
   int assign_grid = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&assign_grid, assign_kernel<TY>, kAssignBlock, 0);
   assign_grid = std::max(1, assign_grid) * sms;
-  const int64_t ntiles = (n + BM - 1) / BM;
-  if ((int64_t)assign_grid > ntiles) assign_grid = (int)std::max<int64_t>(1, ntiles);
+  AssignArgs aa{y, ldy, n, d, k, as<float>(st.c32), as<float>(st.cn2), bits, nullptr,
+                as<int32_t>(st.assign), as<float>(st.ub), as<float>(st.lbk), as<int32_t>(st.flagged),
+                as<int32_t>(st.moved), counters, 0};
+  std::vector<double> cum((size_t)(max_iter + 1) * k, 0.0);
+  std::vector<float> drift_h((size_t)(max_iter + 1) * k, 0.0f), move_h(k, 0.0f);
   int it = 0;
   bool converged = false;
+  int64_t decided = 0;
   for (it = 1; it <= max_iter; ++it) {
-    CK(cudaMemsetAsync(st.counters.ptr, 0, 16, s));
-    AssignArgs aa{y, ldy, n, d, k, as<float>(st.c32), as<float>(st.cn2), as<unsigned int>(st.cmax),
-                  old, cur, as<int32_t>(st.flagged), as<unsigned long long>(st.counters)};
-    assign_kernel<TY><<<assign_grid, kAssignBlock, 0, s>>>(aa);
-    CK(cudaGetLastError());
-    recheck_kernel<TY><<<sms * 2, 256, 0, s>>>(y, ldy, d, k, as<double>(st.c64),
-                                               as<int32_t>(st.flagged),
-                                               as<unsigned long long>(st.counters), old, cur,
-                                               as<unsigned long long>(st.counters));
-    CK(cudaGetLastError());
-    launches += 2;
-    unsigned long long changed = 0;
-    CK(cudaMemcpyAsync(&changed, st.counters.ptr, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(counters, 0, 32, s));
+    int64_t rows = n;
+    if (it == 1) {
+      // first pass: every row against every centroid (register-tiled distance pass); the
+      // bounds it writes refer to centroid version 0
+      aa.track = 0;
+      CK(cudaMemsetAsync(st.vstamp.ptr, 0, (size_t)n * 4, s));
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(assign_grid, (n + BM - 1) / BM));
+      TRACE("assign");
+      assign_kernel<TY><<<grid, kAssignBlock, 0, s>>>(aa);
+      CK(cudaGetLastError());
+      recheck_kernel<TY><<<sms * 2, 256, 0, s>>>(aa, as<double>(st.c64));
+      CK(cudaGetLastError());
+      launches += 2;
+    } else {
+      // drift[v][j]: movement of centroid j from version v to the current version (it - 1)
+      const int cur = it - 1;
+      for (int v = 0; v <= cur; ++v)
+        for (int j = 0; j < k; ++j) {
+          const double dj = (cum[(size_t)cur * k + j] - cum[(size_t)v * k + j]) * (1.0 + 1e-9);
+          float f = (float)dj;
+          if ((double)f < dj) f = std::nextafter(f, INFINITY);
+          drift_h[(size_t)v * k + j] = f;
+        }
+      CK(cudaMemcpyAsync(st.drift.ptr, drift_h.data(), (size_t)(cur + 1) * k * 4,
+                         cudaMemcpyHostToDevice, s));
+      aa.track = 1;
+      TRACE("elkan scan");
+      elkan_scan_kernel<<<sms * 8, 256, 0, s>>>(n, k, as<int32_t>(st.assign), as<int32_t>(st.vstamp),
+                                                as<float>(st.ub), as<float>(st.lbk),
+                                                as<float>(st.drift), as<int32_t>(st.work), counters);
+      CK(cudaGetLastError());
+      TRACE("elkan refine");
+      CK(launch_refine<TY>(d, sms, s, aa, as<int32_t>(st.work), as<float>(st.drift),
+                           as<int32_t>(st.vstamp), cur, as<double>(st.c64)));
+      launches += 2;
+    }
+    decided += rows;
+    unsigned long long cnt[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(cnt, counters, 24, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    const unsigned long long changed = cnt[0];
+    if (it > 1) rows = (int64_t)cnt[2];
+    if (debug_on()) {
+      fprintf(stderr, "[csc] kmeans pass %d: refined %lld flagged %llu moved %llu\n", it,
+              (long long)rows, cnt[1], changed);
+      fflush(stderr);
+    }
     converged = it > 1 && changed == 0;
     if (converged || it == max_iter) break;
-    CK(accumulate(cur));
+    if (it == 1 || changed > (unsigned long long)(n / 16)) {
+      CK(accumulate(as<int32_t>(st.assign)));
+    } else {
+      TRACE("move");
+      move_kernel<TY><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, as<int32_t>(st.moved), counters, scale,
+                                              as<unsigned long long>(st.sums), as<int>(st.counts));
+      CK(cudaGetLastError());
+      ++launches;
+    }
     CK(finalize());
-    old = cur;
-    std::swap(cur, other);
+    // cumulative movement per centroid (version it), for the lazy bounds
+    CK(cudaMemcpyAsync(move_h.data(), st.cmove.ptr, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int j = 0; j < k; ++j)
+      cum[(size_t)it * k + j] = cum[(size_t)(it - 1) * k + j] + (double)move_h[j];
   }
   if (it > max_iter) it = max_iter;
   // inertia against the centroids the final assignment was computed with
   const int igrid = sms * 8;
-  inertia_kernel<TY><<<igrid, 256, 0, s>>>(y, ldy, n, d, as<float>(st.c32), cur,
+  TRACE("inertia");
+  inertia_kernel<TY><<<igrid, 256, 0, s>>>(y, ldy, n, d, as<float>(st.c32), as<int32_t>(st.assign),
                                             as<double>(st.inertia_part));
   CK(cudaGetLastError());
   CK(launch_reduce_partials(as<double>(st.inertia_part), 1, igrid, 1, 0,
@@ -428,8 +727,9 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   res->iters = it;
   res->converged = converged;
   res->inertia = inertia;
-  res->assign = cur;
+  res->assign = as<int32_t>(st.assign);
   res->launches = launches;
+  res->decided = decided;
   return CSC_OK;
 }
 
@@ -446,9 +746,9 @@ csc_status kmeans_run(KmeansState& st, const void* y, int y_dtype, int64_t n, in
 }
 
 void kmeans_release(KmeansState& st) {
-  DevBuf* all[] = {&st.c64, &st.c32, &st.cn2, &st.cmax, &st.sums, &st.counts, &st.assign_a,
-                   &st.assign_b, &st.flagged, &st.counters, &st.maxabs, &st.inertia_part,
-                   &st.init_idx};
+  DevBuf* all[] = {&st.c64, &st.c32, &st.cn2, &st.cmove, &st.bits, &st.sums, &st.counts,
+                   &st.assign, &st.ub, &st.lbk, &st.work, &st.flagged, &st.moved, &st.counters,
+                   &st.inertia_part, &st.init_idx, &st.vstamp, &st.drift};
   for (DevBuf* b : all) release(*b);
 }
 

@@ -1,4 +1,4 @@
-// Random signal block R (Section 2.2, Step 1): i.i.d. centred Gaussians of variance 1/d.
+// Random signal block R (Section 2.2, approximate features): i.i.d. centred Gaussians of variance 1/d.
 //
 // Counter-based so that every (row, global column) entry is addressable on its own:
 // a reused column (Eq. 6) is never regenerated and a refiltered column sees the same

@@ -241,9 +241,27 @@ def test_algorithm1_dynamic_parity_cfg1(gpu_lib, cfg1_graph):
             assert cost == pytest.approx(math.sqrt(h["inertia"]), rel=1e-5)
 
 
+def fp32_floor(lt, r, m, lam, ref):
+    """Error of a plain float32 evaluation of the same recursion against float64: the
+    rounding floor any float32 implementation of the filter meets at this size."""
+    lt32 = lt.astype(np.float32)
+    a32 = cb.filter_coefficients(m, lam).astype(np.float32)
+    t_prev = r.astype(np.float32)
+    t_cur = lt32 @ t_prev
+    out = a32[0] * t_prev + a32[1] * t_cur
+    for j in range(2, m + 1):
+        t_prev, t_cur = t_cur, 2.0 * (lt32 @ t_cur) - t_prev
+        out += a32[j] * t_cur
+    return rel(out, ref)
+
+
 def test_full_size_sampled_columns(gpu_lib):
     """n = 1e6 Zipf SBM (degree 30), 64 columns, m = 100 in the bench's tile configuration;
-    the oracle recomputes two sampled columns in float64 (columns are independent)."""
+    the oracle recomputes two sampled columns in float64 (columns are independent).
+
+    At this size the float32 rounding noise of the recursion, which the low-pass does not
+    damp, is amplified by about sqrt(n/k) relative to the filtered signal; the tolerance is
+    max(1e-5, 2 x the measured float32 floor of the same recursion)."""
     sizes = W.zipf_block_sizes(1_000_000, 100, 0.8)
     g = W.sbm_graph(1_000_000, sizes, 30, 10, seed=2)
     c, d, m, lam = 64, 256, 100, 0.06
@@ -256,7 +274,10 @@ def test_full_size_sampled_columns(gpu_lib):
     lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
     cols = [0, 37]
     ref = cb.cheb_filter(lt, r[:, cols].astype(np.float64), m, lam)
-    assert rel(got[:, cols], ref) < FP32_TOL
+    floor = fp32_floor(lt, r[:, cols], m, lam, ref)
+    err = rel(got[:, cols], ref)
+    print(f"full-size sampled columns: GPU error {err:.3e}, float32 floor {floor:.3e}")
+    assert err < max(FP32_TOL, 2.0 * floor)
     # moment identity at full size: ||Psi||_F^2 from the moments equals the direct norm
     a = cb.filter_coefficients(m, lam)
     i, j = np.meshgrid(np.arange(m + 1), np.arange(m + 1), indexing="ij")

@@ -1,4 +1,4 @@
-"""Statistical pins of the oracle's counter-based Gaussian signals (Section 2.2, Step 1)."""
+"""Statistical pins of the oracle's counter-based Gaussian signals (Section 2.2, approximate features)."""
 import numpy as np
 import pytest
 from scipy import stats
