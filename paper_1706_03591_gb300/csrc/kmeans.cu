@@ -100,38 +100,43 @@ __global__ void update_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, 
 
 // Means from the fixed-point sums (an empty cluster keeps its centroid), the float32 copies,
 // |c32|^2, and for the pruning bounds the movement of every centroid (rounded up) and the
-// largest movement.  One warp per centroid.
+// largest movement.  One block per centroid.
 __global__ void finalize_kernel(const unsigned long long* __restrict__ sums,
                                 const int* __restrict__ counts, int k, int d, double inv_scale,
                                 double* __restrict__ c64, float* __restrict__ c32,
                                 float* __restrict__ cn2, float* __restrict__ cmove,
                                 unsigned int* __restrict__ cmax_bits,
                                 unsigned int* __restrict__ dmax_bits) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < k; j += nw) {
-    const int cnt = counts[j];
-    double mv = 0.0, nrm = 0.0;
-    for (int l = lane; l < d; l += 32) {
-      const size_t e = (size_t)j * d + l;
-      const double old = c64[e];
-      const double nwv = cnt > 0 ? (double)(long long)sums[e] * inv_scale / (double)cnt : old;
-      mv += (nwv - old) * (nwv - old);
-      c64[e] = nwv;
-      const float f = (float)nwv;
-      c32[e] = f;
-      nrm += (double)f * (double)f;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      mv += __shfl_xor_sync(0xffffffffu, mv, off);
-      nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-    }
-    if (lane == 0) {
-      cn2[j] = (float)nrm;
-      const float move = __double2float_ru(sqrt(mv) * (1.0 + 1e-12));
-      cmove[j] = move;
-      atomicMax(cmax_bits, __float_as_uint(__double2float_ru(sqrt(nrm) * (1.0 + 1e-7))));
-      atomicMax(dmax_bits, __float_as_uint(move));
-    }
+  __shared__ double red[2][32];
+  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int cnt = counts[j];
+  const double f = cnt > 0 ? inv_scale / (double)cnt : 0.0;
+  double mv = 0.0, nrm = 0.0;
+  for (int l = threadIdx.x; l < d; l += blockDim.x) {
+    const size_t e = (size_t)j * d + l;
+    const double old = c64[e];
+    const double nwv = cnt > 0 ? (double)(long long)sums[e] * f : old;
+    mv += (nwv - old) * (nwv - old);
+    c64[e] = nwv;
+    const float fv = (float)nwv;
+    c32[e] = fv;
+    nrm += (double)fv * (double)fv;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mv += __shfl_xor_sync(0xffffffffu, mv, off);
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+  }
+  if (lane == 0) { red[0][wid] = mv; red[1][wid] = nrm; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mv = 0.0; nrm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { mv += red[0][w]; nrm += red[1][w]; }
+    cn2[j] = (float)nrm;
+    const float move = __double2float_ru(sqrt(mv) * (1.0 + 1e-12));
+    cmove[j] = move;
+    atomicMax(cmax_bits, __float_as_uint(__double2float_ru(sqrt(nrm) * (1.0 + 1e-7))));
+    atomicMax(dmax_bits, __float_as_uint(move));
   }
 }
 
@@ -462,6 +467,214 @@ __global__ void elkan_refine_kernel(AssignArgs a, const int32_t* __restrict__ wo
   }
 }
 
+// Fused pruned pass for k <= 32*KC, d <= 128*DW4, d a multiple of 4 (16-byte rows): one warp
+// per row, no work list.  The row's bounds (KC per lane) and features (DW4 float4 per lane)
+// are loaded up front; rows whose bounds exclude every other centroid write nothing (their
+// bounds stay lazy).  Distances use f_j = |c_j|^2 - 2 <y, c_j> with the error bound
+// B = u (3.1 cmax^2 + 2 (1.01 d + 1) |y| cmax) of the distance pass (|y|^2 is common to all
+// centroids of the row and cancels in the decision).  The first batch (own centroid plus up to
+// three candidates) tightens ub; the remaining candidates are listed once and measured four
+// at a time.
+__device__ __forceinline__ float4 ld4f(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4f(const __nv_bfloat16* p) {
+  const uint2 raw = *reinterpret_cast<const uint2*>(p);
+  const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+  const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+template <typename TY, int DW4, int KC>
+__global__ void __launch_bounds__(256) elkan_pass_kernel(AssignArgs a, const float* __restrict__ drift,
+                                                         int32_t* __restrict__ vstamp, int version,
+                                                         const double* __restrict__ c64) {
+  __shared__ int clist[8][32 * KC];
+  const TY* __restrict__ y = static_cast<const TY*>(a.y);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float cmax = __uint_as_float(*a.cmax_bits);
+  const float u = 5.9604644775390625e-8f;
+  const int d = a.d, k = a.k;
+  int* cl = clist[wid];
+  for (int64_t row = warp; row < a.n; row += nwarps) {
+    const int asg = a.assign[row];
+    const int vs = vstamp[row];
+    const float ub0 = a.ub[row];
+    float* lrow = a.lbk + row * k;
+    float l[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+      const int j = lane + 32 * i;
+      l[i] = j < k ? __ldcs(lrow + j) : INFINITY;
+    }
+    const float* dv = drift + (size_t)vs * k;
+    float ubv = __fadd_ru(ub0, __ldg(dv + asg));
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+      const int j = lane + 32 * i;
+      if (j < k) l[i] = fmaxf(__fsub_rd(l[i], __ldg(dv + j)), 0.0f);
+      any |= j < k && j != asg && !(ubv < l[i]);
+    }
+    if (!__any_sync(0xffffffffu, any)) continue;  // keeps its centroid; bounds stay lazy
+    // features: lane owns elements 128 t + 4 lane .. +3
+    float4 yv[DW4];
+    float yn = 0.f;
+#pragma unroll
+    for (int t = 0; t < DW4; ++t) {
+      const int e = 128 * t + 4 * lane;
+      yv[t] = e < d ? ld4f(y + row * a.ldy + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      yn = fmaf(yv[t].x, yv[t].x, fmaf(yv[t].y, yv[t].y, fmaf(yv[t].z, yv[t].z, fmaf(yv[t].w, yv[t].w, yn))));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) yn += __shfl_xor_sync(0xffffffffu, yn, off);
+    const float B = u * (3.1f * cmax * cmax + 2.0f * (1.01f * d + 1.0f) * sqrtf(yn) * cmax);
+    const float ey = (d + 2.0f) * u * yn;  // error of yn itself (bounds only)
+    auto measure = [&](const int (&q)[4], int nq, float (&f)[4]) {
+      float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t < nq) {
+          const float* c = a.c32 + (size_t)q[t] * d;
+#pragma unroll
+          for (int w = 0; w < DW4; ++w) {
+            const int e = 128 * w + 4 * lane;
+            if (e < d) {
+              const float4 cv = ld4f(c + e);
+              part[t] = fmaf(yv[w].x, cv.x, fmaf(yv[w].y, cv.y, fmaf(yv[w].z, cv.z, fmaf(yv[w].w, cv.w, part[t]))));
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) part[t] += __shfl_xor_sync(0xffffffffu, part[t], off);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nq) f[t] = fmaf(-2.0f, part[t], __ldg(a.cn2 + q[t]));
+    };
+    float best = INFINITY, second = INFINITY, fa = 0.f;
+    int bi = asg;
+    auto consider = [&](int qq, float f) {
+      if (qq == asg) {
+        fa = f;
+        ubv = __fsqrt_ru(fmaxf(__fadd_ru(__fadd_ru(yn, f), B + ey), 0.0f));  // tightened
+      } else {
+        const float lq = __fsqrt_rd(fmaxf(__fsub_rd(__fadd_rd(yn, f), B + ey), 0.0f));
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+          if (lane == (qq & 31) && i == (qq >> 5)) l[i] = lq;
+      }
+      if (f < best || (f == best && qq < bi)) {
+        second = best; best = f; bi = qq;
+      } else if (f < second) {
+        second = f;
+      }
+    };
+    // batch 0: own centroid + up to three loose candidates (index order)
+    int q[4] = {asg, 0, 0, 0};
+    int nq = 1;
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+      const int j = lane + 32 * i;
+      unsigned mask = __ballot_sync(0xffffffffu, j < k && j != asg && !(ubv < l[i]));
+#pragma unroll
+      for (int t = 1; t < 4; ++t) {
+        if (t == nq && mask) {
+          q[t] = 32 * i + __ffs(mask) - 1;
+          mask &= mask - 1;
+          ++nq;
+        }
+      }
+    }
+    {
+      float f[4];
+      measure(q, nq, f);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nq) consider(q[t], f[t]);
+    }
+    // remaining candidates under the tightened bound, listed once
+    int nc = 0;
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+      const int j = lane + 32 * i;
+      bool cand = j < k && j != asg && !(ubv < l[i]);
+#pragma unroll
+      for (int t = 1; t < 4; ++t) cand &= !(t < nq && j == q[t]);
+      const unsigned mask = __ballot_sync(0xffffffffu, cand);
+      if (cand) cl[nc + __popc(mask & ((1u << lane) - 1u))] = j;
+      nc += __popc(mask);
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < nc; c0 += 4) {
+      int qb[4];
+      const int nb = min(4, nc - c0);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) qb[t] = t < nb ? cl[c0 + t] : 0;
+      float f[4];
+      measure(qb, nb, f);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nb) consider(qb[t], f[t]);
+    }
+    __syncwarp();
+    if (!(second - best > 2.0f * B)) {
+      // near tie: float64 on every centroid whose lower bound still admits the minimum
+      const float limit = __fsqrt_ru(__fadd_ru(__fadd_ru(yn, best), 2.0f * B + ey));
+      double b64 = INFINITY;
+      int b64i = asg;
+      for (int i = 0; i < KC; ++i) {
+        const int j = lane + 32 * i;
+        const bool maybe = j < k && (j == asg || l[i] <= limit);
+        unsigned mask = __ballot_sync(0xffffffffu, maybe);
+        while (mask) {
+          const int qq = 32 * i + __ffs(mask) - 1;
+          mask &= mask - 1;
+          const double* c = c64 + (size_t)qq * d;
+          double sacc = 0.0;
+#pragma unroll
+          for (int w = 0; w < DW4; ++w) {
+            const int e = 128 * w + 4 * lane;
+            if (e < d) {
+              const double d0 = (double)yv[w].x - c[e], d1 = (double)yv[w].y - c[e + 1];
+              const double d2 = (double)yv[w].z - c[e + 2], d3 = (double)yv[w].w - c[e + 3];
+              sacc = fma(d0, d0, fma(d1, d1, fma(d2, d2, fma(d3, d3, sacc))));
+            }
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+          if (sacc < b64 || (sacc == b64 && qq < b64i)) { b64 = sacc; b64i = qq; }
+        }
+      }
+      bi = b64i;
+      best = __fsub_ru((float)b64, yn);  // back to the f scale; bounds below use B + ey slack
+    }
+    // write back the bounds at the current version
+    if (bi != asg) {
+      const float la = __fsqrt_rd(fmaxf(__fsub_rd(__fadd_rd(yn, fa), B + ey), 0.0f));
+#pragma unroll
+      for (int i = 0; i < KC; ++i)
+        if (lane == (asg & 31) && i == (asg >> 5)) l[i] = la;
+    }
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+      const int j = lane + 32 * i;
+      if (j < k) lrow[j] = l[i];
+    }
+    if (lane == 0) {
+      a.ub[row] = __fsqrt_ru(fmaxf(__fadd_ru(__fadd_ru(yn, best), B + ey + 1e-6f * (yn + fabsf(best))), 0.0f));
+      vstamp[row] = version;
+      if (bi != asg) {
+        a.assign[row] = bi;
+        if (a.track) record_move(a, row, asg, bi);
+      }
+    }
+  }
+}
+
 // Applies the fixed-point deltas of the rows that changed cluster: one warp per row.
 template <typename TY>
 __global__ void move_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d,
@@ -550,6 +763,26 @@ cudaError_t launch_refine(int d, int sms, cudaStream_t s, const AssignArgs& aa, 
   return cudaGetLastError();
 }
 
+template <typename TY, int DW4>
+cudaError_t launch_fused_k(int k, int sms, cudaStream_t s, const AssignArgs& aa, const float* drift,
+                           int32_t* vstamp, int version, const double* c64) {
+  const int grid = sms * 8;
+  if (k <= 32)
+    elkan_pass_kernel<TY, DW4, 1><<<grid, 256, 0, s>>>(aa, drift, vstamp, version, c64);
+  else if (k <= 64)
+    elkan_pass_kernel<TY, DW4, 2><<<grid, 256, 0, s>>>(aa, drift, vstamp, version, c64);
+  else
+    elkan_pass_kernel<TY, DW4, 4><<<grid, 256, 0, s>>>(aa, drift, vstamp, version, c64);
+  return cudaGetLastError();
+}
+
+template <typename TY>
+cudaError_t launch_fused(int d, int k, int sms, cudaStream_t s, const AssignArgs& aa,
+                         const float* drift, int32_t* vstamp, int version, const double* c64) {
+  if (d <= 128) return launch_fused_k<TY, 1>(k, sms, s, aa, drift, vstamp, version, c64);
+  return launch_fused_k<TY, 2>(k, sms, s, aa, drift, vstamp, version, c64);
+}
+
 template <typename TY>
 csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy, int k,
                      const int64_t* init_idx, const int32_t* prev_assign, int max_iter,
@@ -625,7 +858,7 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     cudaError_t e = cudaMemsetAsync(st.bits.ptr, 0, 8, s);
     if (e != cudaSuccess) return e;
     ++launches;
-    finalize_kernel<<<1, 1024, 0, s>>>(as<unsigned long long>(st.sums), as<int>(st.counts), k, d,
+    finalize_kernel<<<k, 128, 0, s>>>(as<unsigned long long>(st.sums), as<int>(st.counts), k, d,
                                        inv_scale, as<double>(st.c64), as<float>(st.c32),
                                        as<float>(st.cn2), as<float>(st.cmove), bits, bits + 1);
     return cudaGetLastError();
@@ -672,25 +905,35 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
       CK(cudaMemcpyAsync(st.drift.ptr, drift_h.data(), (size_t)(cur + 1) * k * 4,
                          cudaMemcpyHostToDevice, s));
       aa.track = 1;
-      TRACE("elkan scan");
-      elkan_scan_kernel<<<sms * 8, 256, 0, s>>>(n, k, as<int32_t>(st.assign), as<int32_t>(st.vstamp),
-                                                as<float>(st.ub), as<float>(st.lbk),
-                                                as<float>(st.drift), as<int32_t>(st.work), counters);
-      CK(cudaGetLastError());
-      TRACE("elkan refine");
-      CK(launch_refine<TY>(d, sms, s, aa, as<int32_t>(st.work), as<float>(st.drift),
-                           as<int32_t>(st.vstamp), cur, as<double>(st.c64)));
-      launches += 2;
+      // the fused pass reads rows with 16-byte (8-byte for bf16) vector loads
+      const bool aligned = d % 4 == 0 && ldy % 4 == 0 &&
+                           (reinterpret_cast<uintptr_t>(y) % (4 * sizeof(TY))) == 0;
+      if (k <= 128 && d <= 256 && aligned) {
+        TRACE("elkan pass");
+        CK(launch_fused<TY>(d, k, sms, s, aa, as<float>(st.drift), as<int32_t>(st.vstamp), cur,
+                            as<double>(st.c64)));
+        launches += 1;
+      } else {
+        TRACE("elkan scan");
+        elkan_scan_kernel<<<sms * 8, 256, 0, s>>>(n, k, as<int32_t>(st.assign), as<int32_t>(st.vstamp),
+                                                  as<float>(st.ub), as<float>(st.lbk),
+                                                  as<float>(st.drift), as<int32_t>(st.work), counters);
+        CK(cudaGetLastError());
+        TRACE("elkan refine");
+        CK(launch_refine<TY>(d, sms, s, aa, as<int32_t>(st.work), as<float>(st.drift),
+                             as<int32_t>(st.vstamp), cur, as<double>(st.c64)));
+        launches += 2;
+      }
     }
     decided += rows;
-    unsigned long long cnt[3] = {0, 0, 0};
-    CK(cudaMemcpyAsync(cnt, counters, 24, cudaMemcpyDeviceToHost, s));
+    unsigned long long cnt[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(cnt, counters, 32, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const unsigned long long changed = cnt[0];
     if (it > 1) rows = (int64_t)cnt[2];
     if (debug_on()) {
-      fprintf(stderr, "[csc] kmeans pass %d: refined %lld flagged %llu moved %llu\n", it,
-              (long long)rows, cnt[1], changed);
+      fprintf(stderr, "[csc] kmeans pass %d: refined %lld flagged %llu moved %llu candidates %llu\n",
+              it, (long long)rows, cnt[1], changed, cnt[3]);
       fflush(stderr);
     }
     converged = it > 1 && changed == 0;
