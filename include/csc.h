@@ -50,7 +50,8 @@ typedef enum csc_status {
   CSC_ENOMEM = 2,   /* a device or host allocation failed */
   CSC_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
   CSC_ETIMEOUT = 4, /* a bounded device-side wait expired */
-  CSC_ESTATE = 5    /* call order: e.g. csc_filter before csc_set_graph */
+  CSC_ESTATE = 5,   /* call order: e.g. csc_filter before csc_set_graph */
+  CSC_ELIMIT = 6    /* a size is beyond the fixed limit of csc_cheb_filter_noalloc */
 } csc_status;
 
 enum { CSC_HOST = 0, CSC_DEVICE = 1 };
@@ -221,6 +222,33 @@ csc_status csc_get_moments(csc_ctx* ctx, double* mu_out, int len);
  * iters_out = Lloyd assignment passes.  Outputs may be NULL except assign_out. */
 csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_idx,
                        int32_t* assign_out, int where, double* cost_out, int* iters_out);
+
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory while they run (code inside a CUDA stream capture, programs whose
+ * caching allocator owns all device memory, services that forbid allocation after start-up).
+ *
+ * Computes the same Psi~ = h(L) R and trace moments as csc_cheb_filter, for a graph given
+ * directly as caller-owned device CSR (row_ptr int64[n+1], col_idx int32[nnz], vals float[nnz]
+ * or NULL; valid symmetric CSR as described at csc_set_graph, not validated here), a
+ * caller-owned device signal block R (float32, n x c, leading dimension ldr >= c) and a
+ * caller-owned device output psi_out (float32, n x c, leading dimension ldp >= c; NULL:
+ * moments only).  mu_out: host double[2m+1] or NULL.  Work runs on cuda_stream (NULL = default
+ * stream); the call returns when the results are written.
+ *
+ * It allocates nothing: all scratch lives in one fixed static device array of about 11 MB,
+ * which every GPU that loads this library holds until the process exits.  Limits: n <= 65,536,
+ * nnz <= 4,194,304, 1 <= m <= 128 (any c; columns are processed 8 at a time); larger sizes
+ * return CSC_ELIMIT.  The first call on a device looks up that array's device address (which
+ * loads the module), so make the first call before any stream capture.  Every call shares the
+ * one array: calls that overlap on the GPU (other streams or host threads) race on it and must
+ * be serialised by the caller.  Errors: CSC_EINVAL (bad pointers or sizes), CSC_ELIMIT,
+ * CSC_ECUDA. */
+csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                   const int32_t* col_idx, const float* vals, int m,
+                                   double lambda_c, const float* R, int c, int64_t ldr,
+                                   float* psi_out, int64_t ldp, double* mu_out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

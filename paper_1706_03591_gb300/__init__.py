@@ -20,7 +20,7 @@ __all__ = [
     "csc_filter_coeffs", "csc_count_tolerance", "csc_count_from_moments",
     "csc_lambda_search_moments", "csc_signals", "csc_cheb_filter", "csc_kmeans",
     "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
-    "csc_abi_version", "csc_get_stats",
+    "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc",
 ]
 
 
@@ -218,6 +218,28 @@ def csc_cluster(h, k: int, seed: int, init_idx, assign_out):
     _check(_lib().csc_cluster(h, k, seed, None if idx is None else C.c_void_p(idx.ctypes.data), ap, aw,
                               C.byref(cost), C.byref(iters)), h, "csc_cluster")
     return cost.value, iters.value
+
+
+def csc_cheb_filter_noalloc(n: int, row_ptr, col_idx, vals, m: int, lambda_c: float, R,
+                            psi_out=None, want_moments: bool = True, stream=None):
+    """Allocation-free filter of a device signal block R over a device CSR graph (small
+    graphs only; see include/csc.h).  Returns the 2m+1 trace moments (or None)."""
+    rp, w1, _, _ = _arr(row_ptr, "row_ptr")
+    ci, w2, _, _ = _arr(col_idx, "col_idx")
+    vv, _, _, _ = _arr(vals, "vals")
+    r, w3, _, ldr = _arr(R, "R")
+    pp, _, _, ldp = _arr(psi_out, "psi_out")
+    c = int(R.shape[1])
+    nnz = int(col_idx.numel() if _is_torch(col_idx) else np.asarray(col_idx).size)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    mu = np.zeros(2 * m + 1) if want_moments else None
+    _check(_lib().csc_cheb_filter_noalloc(
+        n, nnz, rp, ci, vv, m, lambda_c, r, c, ldr or c, pp, ldp or c,
+        mu.ctypes.data_as(C.POINTER(C.c_double)) if mu is not None else None, C.c_void_p(stream or 0)),
+        None, "csc_cheb_filter_noalloc")
+    return mu
 
 
 class Context:

@@ -10,7 +10,7 @@ import os
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcsc.so")
 
-CSC_OK, CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA, CSC_ETIMEOUT, CSC_ESTATE = range(6)
+CSC_OK, CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA, CSC_ETIMEOUT, CSC_ESTATE, CSC_ELIMIT = range(7)
 CSC_HOST, CSC_DEVICE = 0, 1
 CSC_F32, CSC_BF16 = 0, 1
 
@@ -64,6 +64,8 @@ SIGNATURES = {
     "csc_get_features": (_i32, [_p, _p, _i32, _i64, _i32, _i32]),
     "csc_get_moments": (_i32, [_p, _pd, _i32]),
     "csc_cluster": (_i32, [_p, _i32, _u64, _p, _p, _i32, _pd, _pi]),
+    "csc_cheb_filter_noalloc": (_i32, [_i64, _i64, _p, _p, _p, _i32, _dbl, _p, _i32, _i64, _p, _i64,
+                                       _pd, _p]),
 }
 
 _lib = None

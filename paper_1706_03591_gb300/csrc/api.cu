@@ -409,6 +409,7 @@ const char* csc_status_string(csc_status s) {
     case CSC_ECUDA: return "CUDA error";
     case CSC_ETIMEOUT: return "device wait timed out";
     case CSC_ESTATE: return "invalid call order";
+    case CSC_ELIMIT: return "size beyond the fixed limit of the allocation-free entry point";
   }
   return "unknown status";
 }
