@@ -80,6 +80,9 @@ typedef struct csc_stats {
   double step_ms;         /* device time of those launches (ms), CUDA events on the context stream */
   int64_t filter_passes;  /* recursion passes (one per column tile per filtering call) */
   int64_t tile;           /* column-tile width of the last filtering pass */
+  int64_t batched_launches; /* persistent batched kernel launches (direct or in a graph) */
+  int64_t graph_replays;    /* batched launches replayed from a captured CUDA graph */
+  int64_t autotune_trials;  /* candidate tile timings run by the batched-path autotuner */
 } csc_stats;
 
 /* ---------------------------------------------------------------- library */
@@ -222,6 +225,36 @@ csc_status csc_get_moments(csc_ctx* ctx, double* mu_out, int len);
  * iters_out = Lloyd assignment passes.  Outputs may be NULL except assign_out. */
 csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_idx,
                        int32_t* assign_out, int where, double* cost_out, int* iters_out);
+
+/* ---------------------------------------------------------------- batching */
+
+/* One graph of a batched filtering call (all pointers are caller-owned device memory). */
+typedef struct csc_graph_desc {
+  int64_t n;              /* nodes */
+  int64_t nnz;            /* stored entries (both directions of every edge) */
+  const int64_t* row_ptr; /* CSR row pointers, n+1 */
+  const int32_t* col_idx; /* CSR columns, nnz */
+  const float* vals;      /* edge weights, nnz, or NULL for unit weights */
+  int c;                  /* signals filtered for this graph (columns) */
+  int d;                  /* the signals have variance 1/d (d >= c) */
+  double lambda_c;        /* cutoff in [0, 2] */
+  uint64_t seed;          /* signal stream: global column ids 0..c-1 under this key */
+  float* psi;             /* output n x c float32, leading dimension ldp (NULL: moments only) */
+  int64_t ldp;
+} csc_graph_desc;
+
+/* Filters many independent graphs (and snapshots) at once: for every graph g,
+ * Psi~_g = h_g(L_g) R_g with R_g its counter-based signals (stored in bfloat16 when the
+ * context precision is CSC_BF16, else float32), the order-m Jackson-damped low-pass of
+ * cutoff lambda_c, and its trace moments (Sections 2.2 and 3.3).  All recursion steps of all
+ * graphs run in one persistent cooperative kernel launch with bounded grid barriers between
+ * steps, captured in a CUDA graph and replayed on later calls with the same plan.  The
+ * column tile of each graph is chosen by an autotuner that times the candidate tiles once per
+ * graph size class (cached on the context).  Graphs must satisfy the CSR conditions of
+ * csc_set_graph (not validated here).  mu_out: host double[n_graphs * (2m+1)] or NULL.
+ * Errors: CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA, CSC_ETIMEOUT (a grid barrier wait expired). */
+csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_graph_desc* descs, int m,
+                              double* mu_out);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 

@@ -20,7 +20,7 @@ __all__ = [
     "csc_filter_coeffs", "csc_count_tolerance", "csc_count_from_moments",
     "csc_lambda_search_moments", "csc_signals", "csc_cheb_filter", "csc_kmeans",
     "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
-    "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc",
+    "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
 ]
 
 
@@ -102,7 +102,8 @@ def csc_get_stats(h, reset: bool = False) -> dict:
     st = _abi.csc_stats()
     _check(_lib().csc_get_stats(h, C.byref(st), int(reset)), h, "csc_get_stats")
     return dict(launches=st.launches, step_launches=st.step_launches, step_ms=st.step_ms,
-                filter_passes=st.filter_passes, tile=st.tile)
+                filter_passes=st.filter_passes, tile=st.tile, batched_launches=st.batched_launches,
+                graph_replays=st.graph_replays, autotune_trials=st.autotune_trials)
 
 
 def csc_set_graph(h, n: int, row_ptr, col_idx, vals=None) -> None:
@@ -220,6 +221,32 @@ def csc_cluster(h, k: int, seed: int, init_idx, assign_out):
     return cost.value, iters.value
 
 
+def csc_filter_batched(h, graphs, m: int, want_moments: bool = True):
+    """Filters many graphs in one persistent launch.  ``graphs`` is a list of dicts with keys
+    n, row_ptr, col_idx (device tensors), vals (device tensor or None), c, d, lambda_c, seed,
+    psi (device float32 tensor n x c or None).  Returns the moments, shape (len(graphs), 2m+1)."""
+    descs = (_abi.csc_graph_desc * len(graphs))()
+    for i, g in enumerate(graphs):
+        dsc = descs[i]
+        dsc.n = int(g["n"])
+        dsc.nnz = int(g["col_idx"].numel())
+        dsc.row_ptr = g["row_ptr"].data_ptr()
+        dsc.col_idx = g["col_idx"].data_ptr() if g["col_idx"].numel() else None
+        dsc.vals = g["vals"].data_ptr() if g.get("vals") is not None else None
+        dsc.c = int(g["c"])
+        dsc.d = int(g.get("d", g["c"]))
+        dsc.lambda_c = float(g["lambda_c"])
+        dsc.seed = int(g["seed"])
+        psi = g.get("psi")
+        dsc.psi = psi.data_ptr() if psi is not None else None
+        dsc.ldp = int(psi.stride(0)) if psi is not None else int(g["c"])
+    mu = np.zeros((len(graphs), 2 * m + 1)) if want_moments else None
+    _check(_lib().csc_filter_batched(h, len(graphs), descs, m,
+                                     mu.ctypes.data_as(C.POINTER(C.c_double)) if mu is not None else None),
+           h, "csc_filter_batched")
+    return mu
+
+
 def csc_cheb_filter_noalloc(n: int, row_ptr, col_idx, vals, m: int, lambda_c: float, R,
                             psi_out=None, want_moments: bool = True, stream=None):
     """Allocation-free filter of a device signal block R over a device CSR graph (small
@@ -264,6 +291,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def filter_batched(self, graphs, m, want_moments=True):
+        return csc_filter_batched(self.h, graphs, m, want_moments)
 
     def stats(self, reset=False):
         return csc_get_stats(self.h, reset)

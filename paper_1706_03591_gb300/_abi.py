@@ -34,6 +34,25 @@ class csc_stats(C.Structure):
         ("step_ms", C.c_double),
         ("filter_passes", C.c_int64),
         ("tile", C.c_int64),
+        ("batched_launches", C.c_int64),
+        ("graph_replays", C.c_int64),
+        ("autotune_trials", C.c_int64),
+    ]
+
+
+class csc_graph_desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("nnz", C.c_int64),
+        ("row_ptr", C.c_void_p),
+        ("col_idx", C.c_void_p),
+        ("vals", C.c_void_p),
+        ("c", C.c_int),
+        ("d", C.c_int),
+        ("lambda_c", C.c_double),
+        ("seed", C.c_uint64),
+        ("psi", C.c_void_p),
+        ("ldp", C.c_int64),
     ]
 
 
@@ -64,6 +83,7 @@ SIGNATURES = {
     "csc_get_features": (_i32, [_p, _p, _i32, _i64, _i32, _i32]),
     "csc_get_moments": (_i32, [_p, _pd, _i32]),
     "csc_cluster": (_i32, [_p, _i32, _u64, _p, _p, _i32, _pd, _pi]),
+    "csc_filter_batched": (_i32, [_p, _i32, _p, _i32, _pd]),
     "csc_cheb_filter_noalloc": (_i32, [_i64, _i64, _p, _p, _p, _i32, _dbl, _p, _i32, _i64, _p, _i64,
                                        _pd, _p]),
 }

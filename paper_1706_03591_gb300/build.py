@@ -35,7 +35,7 @@ def sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    return sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [
+    return sources() + sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))) + [
         os.path.join(ROOT, "include", "csc.h"), os.path.abspath(__file__)]
 
 

@@ -15,48 +15,6 @@
 
 using csc::DevBuf;
 
-struct csc_ctx {
-  csc_opts opts;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  std::string err;
-  csc::Graph g;
-  // filtering
-  DevBuf tbuf[3];
-  DevBuf psi;
-  DevBuf part;
-  DevBuf ef;          // reduced E/F sums, double[2m+1]
-  DevBuf coef;        // float[m+1]
-  DevBuf rstage;      // caller signal block staged on the device
-  std::vector<double> mu;
-  int last_m = 0;
-  // feature ring (Eq. 6)
-  int64_t ring_n = 0;
-  int ring_d = 0;
-  DevBuf theta;       // float n x d
-  DevBuf y;           // n x d, float or bf16 (row-normalised features)
-  DevBuf slot_src;    // int[d]
-  std::vector<int64_t> stamp;
-  int64_t t = 0;
-  int64_t next_id = 0;
-  bool has_lambda = false;
-  double lambda = 0.0;
-  // k-means
-  csc::KmeansState km;
-  DevBuf prev_assign;
-  int prev_k = 0;
-  bool has_prev = false;
-  DevBuf ystage;      // caller features staged on the device
-  DevBuf astage;      // caller assignment staged on the device
-  DevBuf out_stage;   // conversions before a host copy
-  DevBuf bad;         // CSR violation counter
-  // counters (csc_get_stats)
-  int64_t launches = 0, step_launches = 0, filter_passes = 0;
-  double step_ms = 0.0;
-  int last_tile = 0;
-  std::vector<cudaEvent_t> events;  // timing event pairs, one per column tile
-};
-
 namespace csc {
 
 bool ensure(DevBuf& b, size_t bytes) {
@@ -217,11 +175,11 @@ csc_status fail(csc_ctx* ctx, csc_status s, const std::string& msg) {
 
 int tile_width(const csc_ctx* ctx, int64_t n, int c) {
   if (ctx->opts.col_tile > 0) return ctx->opts.col_tile;
-  // Large graphs: narrow tiles keep the gathered block of one tile near L2 size.
-  const double block_bytes = (double)n * 4.0;
+  // The gather of a row is 4w contiguous bytes: wide rows keep more bytes in flight per
+  // request, which measured faster than L2-sized narrow tiles on the at-scale workload.
+  (void)n;
   int w = 8;
-  while (w < 128 && w < c) w *= 2;
-  while (w > 8 && block_bytes * w * 3.0 > 96.0e6) w /= 2;
+  while (w < 64 && w < c) w *= 2;
   return w;
 }
 
@@ -443,11 +401,15 @@ void csc_destroy(csc_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  if (ctx->b_exec) cudaGraphExecDestroy(ctx->b_exec);
+  if (ctx->b_cap) cudaStreamDestroy(ctx->b_cap);
   DevBuf* bufs[] = {&ctx->g.row_ptr, &ctx->g.col, &ctx->g.val, &ctx->g.scale, &ctx->g.deg,
                     &ctx->g.blk_row, &ctx->g.vs, &ctx->g.ivs,
                     &ctx->tbuf[0], &ctx->tbuf[1], &ctx->tbuf[2], &ctx->psi, &ctx->part, &ctx->ef,
                     &ctx->coef, &ctx->rstage, &ctx->theta, &ctx->y, &ctx->slot_src,
-                    &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad};
+                    &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad,
+                    &ctx->b_prep, &ctx->b_tbuf, &ctx->b_psi, &ctx->b_coef, &ctx->b_mom,
+                    &ctx->b_tiles, &ctx->b_items, &ctx->b_bar, &ctx->b_tune, &ctx->b_part};
   for (DevBuf* b : bufs) csc::release(*b);
   csc::kmeans_release(ctx->km);
   delete ctx;
@@ -462,8 +424,12 @@ csc_status csc_get_stats(csc_ctx* ctx, csc_stats* out, int reset) {
   out->step_ms = ctx->step_ms;
   out->filter_passes = ctx->filter_passes;
   out->tile = ctx->last_tile;
+  out->batched_launches = ctx->batched_launches;
+  out->graph_replays = ctx->graph_replays;
+  out->autotune_trials = ctx->autotune_trials;
   if (reset) {
     ctx->launches = ctx->step_launches = ctx->filter_passes = 0;
+    ctx->batched_launches = ctx->graph_replays = ctx->autotune_trials = 0;
     ctx->step_ms = 0.0;
   }
   return CSC_OK;

@@ -25,6 +25,7 @@
 // epilogue (recursion, Psi update, dot products).  CTAs stride over the blocks of a grid
 // sized to fill every SM.
 #include "csc_internal.h"
+#include "philox.cuh"
 
 namespace csc {
 
@@ -33,9 +34,11 @@ namespace {
 constexpr int kBlock = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// Loads of the recursion blocks and of Psi bypass L1 (cache at L2 only): a block written by
+// one step is read by other SMs in the next, and within a persistent launch L1 is not coherent.
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
-  const uint2 raw = *reinterpret_cast<const uint2*>(p);
+  const uint2 raw = __ldcg(reinterpret_cast<const uint2*>(p));
   const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
   const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
   const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
@@ -181,49 +184,54 @@ __device__ __forceinline__ void block_store(double (&acc)[NQ], double* part) {
   }
 }
 
+// One edge block of the first step: T_1 = L~ T_0 (stored as V_1), Psi = a_0 T_0 + a_1 T_1,
+// partials <T0,T0>, <T1,T1>, <T1,T0> accumulated into acc (lane-0 values).
 template <int LPR, typename T0>
-__global__ void __launch_bounds__(kBlock) cheb_first_kernel(StepArgs a) {
-  __shared__ Stage st;
+__device__ __forceinline__ void first_block(const StepArgs& a, Stage& st, int b, double (&acc)[3]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int slot = lane / LPR, sub = lane % LPR;
   const T0* __restrict__ t0 = static_cast<const T0*>(a.tg);
   const int w = a.w;
   float a0 = 0.f, a1 = 0.f;
   if (a.psi != nullptr) { a0 = __ldg(a.coef); a1 = __ldg(a.coef + 1); }
-  double acc[3] = {0.0, 0.0, 0.0};  // <T0,T0>, <T1,T1>, <T1,T0>
-  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) {
-    int rs, re;
-    __syncthreads();
-    const bool staged = stage_block<true>(a, st, b, rs, re);
-    __syncthreads();
-    for (int r = rs + wid; r < re; r += kBlock / 32) {
-      const int64_t row = r;
-      float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (slot == 0) own = ld4(t0 + row * w + sub * 4);
-      const float si = -__ldg(a.scale + row);
-      const float vsi = __ldg(a.vs + row);
-      const float4 g = gather_row<LPR, true, T0>(a, st, staged, t0, row, r - rs, slot, sub);
-      float e0 = 0.f, e1 = 0.f, f1 = 0.f;
-      if (slot == 0) {
-        const float4 t1 = make_float4(si * g.x, si * g.y, si * g.z, si * g.w);
-        st4(a.tn + row * w + sub * 4, make_float4(vsi * t1.x, vsi * t1.y, vsi * t1.z, vsi * t1.w));
-        if (a.psi != nullptr) {
-          float4 p;
-          p.x = fmaf(a1, t1.x, a0 * own.x);
-          p.y = fmaf(a1, t1.y, a0 * own.y);
-          p.z = fmaf(a1, t1.z, a0 * own.z);
-          p.w = fmaf(a1, t1.w, a0 * own.w);
-          st4(a.psi + row * a.ldp + sub * 4, p);
-        }
-        e0 = dot4(own, own);
-        e1 = dot4(t1, t1);
-        f1 = dot4(t1, own);
+  int rs, re;
+  __syncthreads();
+  const bool staged = stage_block<true>(a, st, b, rs, re);
+  __syncthreads();
+  for (int r = rs + wid; r < re; r += kBlock / 32) {
+    const int64_t row = r;
+    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (slot == 0) own = ld4(t0 + row * w + sub * 4);
+    const float si = -__ldg(a.scale + row);
+    const float vsi = __ldg(a.vs + row);
+    const float4 g = gather_row<LPR, true, T0>(a, st, staged, t0, row, r - rs, slot, sub);
+    float e0 = 0.f, e1 = 0.f, f1 = 0.f;
+    if (slot == 0) {
+      const float4 t1 = make_float4(si * g.x, si * g.y, si * g.z, si * g.w);
+      st4(a.tn + row * w + sub * 4, make_float4(vsi * t1.x, vsi * t1.y, vsi * t1.z, vsi * t1.w));
+      if (a.psi != nullptr) {
+        float4 p;
+        p.x = fmaf(a1, t1.x, a0 * own.x);
+        p.y = fmaf(a1, t1.y, a0 * own.y);
+        p.z = fmaf(a1, t1.z, a0 * own.z);
+        p.w = fmaf(a1, t1.w, a0 * own.w);
+        st4(a.psi + row * a.ldp + sub * 4, p);
       }
-      fold_dot<LPR>(e0, acc[0], lane);
-      fold_dot<LPR>(e1, acc[1], lane);
-      fold_dot<LPR>(f1, acc[2], lane);
+      e0 = dot4(own, own);
+      e1 = dot4(t1, t1);
+      f1 = dot4(t1, own);
     }
+    fold_dot<LPR>(e0, acc[0], lane);
+    fold_dot<LPR>(e1, acc[1], lane);
+    fold_dot<LPR>(f1, acc[2], lane);
   }
+}
+
+template <int LPR, typename T0>
+__global__ void __launch_bounds__(kBlock) cheb_first_kernel(StepArgs a) {
+  __shared__ Stage st;
+  double acc[3] = {0.0, 0.0, 0.0};  // <T0,T0>, <T1,T1>, <T1,T0>
+  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) first_block<LPR, T0>(a, st, b, acc);
   block_store<3>(acc, a.part);
 }
 
@@ -271,9 +279,11 @@ __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const Stage&
   return acc;
 }
 
+// One edge block of a general step (row-parallel: the LPR lanes of a slot own a row):
+// V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1}, Psi += a_{j+1} T_{j+1}; partials
+// <T_{j+1},T_{j+1}>, <T_{j+1},T_j> accumulated into acc (first lane of each slot).
 template <int LPR, typename TP>
-__global__ void __launch_bounds__(kBlock, 3) cheb_step_kernel(StepArgs a) {
-  __shared__ Stage st;
+__device__ __forceinline__ void step_block(const StepArgs& a, Stage& st, int b, double (&acc)[2]) {
   constexpr int S = 32 / LPR;
   constexpr int kRowsPerPass = (kBlock / 32) * S;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -282,62 +292,64 @@ __global__ void __launch_bounds__(kBlock, 3) cheb_step_kernel(StepArgs a) {
   const TP* __restrict__ tp = static_cast<const TP*>(a.tp);
   const int w = a.w;
   const float aj = a.psi != nullptr ? __ldg(a.coef + a.j + 1) : 0.f;
-  double acc[2] = {0.0, 0.0};  // <T_{j+1},T_{j+1}>, <T_{j+1},T_j>
-  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) {
-    int rs, re;
-    __syncthreads();
-    const bool staged = stage_block<false>(a, st, b, rs, re);
-    __syncthreads();
-    for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
-      const int r = r0 + wid * S + slot;
-      const bool valid = r < re;
-      const int64_t row = valid ? r : rs;
-      // own-row operands are independent of the gather: issue them first
-      float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), own = prev, p = prev;
-      float vsi = 1.f, ivsi = 1.f;
-      if (valid) {
-        vsi = __ldg(a.vs + row);
-        ivsi = __ldg(a.ivs + row);
-        prev = ld4(tp + row * w + sub * 4);
-        own = ld4(tg + row * w + sub * 4);
-        if (a.psi != nullptr) p = ld4(a.psi + row * a.ldp + sub * 4);
+  int rs, re;
+  __syncthreads();
+  const bool staged = stage_block<false>(a, st, b, rs, re);
+  __syncthreads();
+  for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
+    const int r = r0 + wid * S + slot;
+    const bool valid = r < re;
+    const int64_t row = valid ? r : rs;
+    // own-row operands are independent of the gather: issue them first
+    float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), own = prev, p = prev;
+    float vsi = 1.f, ivsi = 1.f;
+    if (valid) {
+      vsi = __ldg(a.vs + row);
+      ivsi = __ldg(a.ivs + row);
+      prev = ld4(tp + row * w + sub * 4);
+      own = ld4(tg + row * w + sub * 4);
+      if (a.psi != nullptr) p = ld4(a.psi + row * a.ldp + sub * 4);
+    }
+    const float4 g = gather_own_row<LPR>(a, st, staged, tg, row, r - rs, valid, sub);
+    float e = 0.f, f = 0.f;
+    if (valid) {
+      const float c2 = -2.0f * vsi * vsi;
+      if (a.tp_unscaled) { prev.x *= vsi; prev.y *= vsi; prev.z *= vsi; prev.w *= vsi; }
+      float4 v;
+      v.x = fmaf(c2, g.x, -prev.x);
+      v.y = fmaf(c2, g.y, -prev.y);
+      v.z = fmaf(c2, g.z, -prev.z);
+      v.w = fmaf(c2, g.w, -prev.w);
+      st4(a.tn + row * w + sub * 4, v);
+      const float4 t = make_float4(v.x * ivsi, v.y * ivsi, v.z * ivsi, v.w * ivsi);
+      const float4 tc = make_float4(own.x * ivsi, own.y * ivsi, own.z * ivsi, own.w * ivsi);
+      if (a.psi != nullptr) {
+        p.x = fmaf(aj, t.x, p.x);
+        p.y = fmaf(aj, t.y, p.y);
+        p.z = fmaf(aj, t.z, p.z);
+        p.w = fmaf(aj, t.w, p.w);
+        st4(a.psi + row * a.ldp + sub * 4, p);
       }
-      const float4 g = gather_own_row<LPR>(a, st, staged, tg, row, r - rs, valid, sub);
-      float e = 0.f, f = 0.f;
-      if (valid) {
-        // V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1};  T = V / vs
-        const float c2 = -2.0f * vsi * vsi;
-        if (a.tp_unscaled) { prev.x *= vsi; prev.y *= vsi; prev.z *= vsi; prev.w *= vsi; }
-        float4 v;
-        v.x = fmaf(c2, g.x, -prev.x);
-        v.y = fmaf(c2, g.y, -prev.y);
-        v.z = fmaf(c2, g.z, -prev.z);
-        v.w = fmaf(c2, g.w, -prev.w);
-        st4(a.tn + row * w + sub * 4, v);
-        const float4 t = make_float4(v.x * ivsi, v.y * ivsi, v.z * ivsi, v.w * ivsi);
-        const float4 tc = make_float4(own.x * ivsi, own.y * ivsi, own.z * ivsi, own.w * ivsi);
-        if (a.psi != nullptr) {
-          p.x = fmaf(aj, t.x, p.x);
-          p.y = fmaf(aj, t.y, p.y);
-          p.z = fmaf(aj, t.z, p.z);
-          p.w = fmaf(aj, t.w, p.w);
-          st4(a.psi + row * a.ldp + sub * 4, p);
-        }
-        e = dot4(t, t);
-        f = dot4(t, tc);
-      }
-      // fold over the LPR lanes of the slot; its first lane accumulates in float64
+      e = dot4(t, t);
+      f = dot4(t, tc);
+    }
 #pragma unroll
-      for (int off = 1; off < LPR; off <<= 1) {
-        e += __shfl_xor_sync(kFull, e, off);
-        f += __shfl_xor_sync(kFull, f, off);
-      }
-      if (sub == 0 && valid) {
-        acc[0] += (double)e;
-        acc[1] += (double)f;
-      }
+    for (int off = 1; off < LPR; off <<= 1) {
+      e += __shfl_xor_sync(kFull, e, off);
+      f += __shfl_xor_sync(kFull, f, off);
+    }
+    if (sub == 0 && valid) {
+      acc[0] += (double)e;
+      acc[1] += (double)f;
     }
   }
+}
+
+template <int LPR, typename TP>
+__global__ void __launch_bounds__(kBlock, 3) cheb_step_kernel(StepArgs a) {
+  __shared__ Stage st;
+  double acc[2] = {0.0, 0.0};  // <T_{j+1},T_{j+1}>, <T_{j+1},T_j>
+  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) step_block<LPR, TP>(a, st, b, acc);
   // every lane may hold a partial: reduce the warp first
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -345,6 +357,132 @@ __global__ void __launch_bounds__(kBlock, 3) cheb_step_kernel(StepArgs a) {
     acc[1] += __shfl_xor_sync(kFull, acc[1], off);
   }
   block_store<2>(acc, a.part);
+}
+
+// ------------------------------------------------------------------ batched filtering
+
+// Grid barrier for a cooperative launch (all blocks co-resident).  Sense by generation
+// counter; the wait is bounded (about a second), after which *err is set and false returned.
+__device__ bool grid_barrier(unsigned int* bar, int* err) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > (1ll << 23) || *(volatile int*)err != 0) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    ok = *(volatile int*)err == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int NQ>
+__device__ __forceinline__ void block_atomic(double (&acc)[NQ], double* dst) {
+  __shared__ double red[NQ][kBlock / 32];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[q][wid] = acc[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double v = 0.0;
+    for (int i = 0; i < kBlock / 32; ++i) v += red[threadIdx.x][i];
+    atomicAdd(dst + threadIdx.x, v);
+  }
+}
+
+template <int LPR>
+__device__ void batched_signals(const BatchTile& t, int b) {
+  const int rs = __ldg(t.a.blk_row + b), re = __ldg(t.a.blk_row + b + 1);
+  const int w = t.a.w;
+  const uint32_t k0 = (uint32_t)t.seed, k1 = (uint32_t)(t.seed >> 32);
+  for (int e = threadIdx.x; e < (re - rs) * w; e += blockDim.x) {
+    const int64_t row = rs + e / w;
+    const int v = e % w;
+    float val = 0.0f;
+    if (v < t.valid) val = gauss_signal((uint64_t)row, (uint64_t)(t.col0 + v), k0, k1) * t.inv_sqrt_d;
+    if (t.t0_dtype == CSC_BF16)
+      static_cast<__nv_bfloat16*>(t.buf[0])[row * w + v] = __float2bfloat16_rn(val);
+    else
+      static_cast<float*>(t.buf[0])[row * w + v] = val;
+  }
+}
+
+template <int LPR>
+__device__ void batched_item(const BatchTile& t, Stage& st, int b, int s) {
+  StepArgs a = t.a;
+  if (s == 1) {
+    a.tg = t.buf[0];
+    a.tn = static_cast<float*>(t.buf[1]);
+    a.j = 0;
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (t.t0_dtype == CSC_BF16) first_block<LPR, __nv_bfloat16>(a, st, b, acc);
+    else first_block<LPR, float>(a, st, b, acc);
+    // first-step rows of the E/F table: E0, E1, F1
+    block_atomic<3>(acc, t.mom);
+  } else {
+    const int j = s - 1;  // produces T_{j+1}
+    a.tg = t.buf[j % 3];
+    a.tp = t.buf[(j - 1) % 3];
+    a.tn = static_cast<float*>(t.buf[(j + 1) % 3]);
+    a.j = j;
+    a.tp_unscaled = j == 1;
+    double acc[2] = {0.0, 0.0};
+    if (j == 1 && t.t0_dtype == CSC_BF16) step_block<LPR, __nv_bfloat16>(a, st, b, acc);
+    else step_block<LPR, float>(a, st, b, acc);
+    block_atomic<2>(acc, t.mom + 2 * (j + 1) - 1);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 2) cheb_batched_kernel(const BatchTile* __restrict__ tiles,
+                                                                 const int32_t* __restrict__ item_tile,
+                                                                 int64_t nitems, int m,
+                                                                 unsigned int* bar, int* err) {
+  __shared__ Stage st;
+  for (int s = 0; s <= m; ++s) {
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+      const int ti = __ldg(item_tile + it);
+      const BatchTile& t = tiles[ti];
+      const int b = (int)(it - t.blk0);
+      if (s == 0) {
+        switch (t.lpr) {
+          case 2: batched_signals<2>(t, b); break;
+          case 4: batched_signals<4>(t, b); break;
+          case 8: batched_signals<8>(t, b); break;
+          default: batched_signals<16>(t, b); break;
+        }
+      } else {
+        switch (t.lpr) {
+          case 2: batched_item<2>(t, st, b, s); break;
+          case 4: batched_item<4>(t, st, b, s); break;
+          case 8: batched_item<8>(t, st, b, s); break;
+          default: batched_item<16>(t, st, b, s); break;
+        }
+      }
+    }
+    if (!grid_barrier(bar, err)) return;
+  }
 }
 
 template <typename T0>
@@ -423,6 +561,25 @@ cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStre
   const void* fn = tp_dtype == CSC_BF16 ? step_kernel_for<__nv_bfloat16>(lpr)
                                         : step_kernel_for<float>(lpr);
   return launch_any(fn, a, grid, s);
+}
+
+int cheb_batched_grid() {
+  static int grid = 0;
+  if (grid == 0) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_batched_kernel, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    grid = per_sm * num_sms();
+  }
+  return grid;
+}
+
+cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, int64_t nitems,
+                                int m, unsigned int* barrier, int* err, int grid, cudaStream_t s) {
+  void* args[] = {(void*)&tiles, (void*)&item_tile, (void*)&nitems, (void*)&m, (void*)&barrier,
+                  (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)cheb_batched_kernel, dim3(grid), dim3(kBlock), args,
+                                     0, s);
 }
 
 cudaError_t launch_reduce_partials(const double* part, int nrows, int grid, int tiles,

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -108,6 +109,27 @@ cudaError_t launch_cheb_first(const StepArgs& a, int t0_dtype, int grid, cudaStr
 // {<T_{j+1},T_{j+1}>, <T_{j+1},T_j>}.  tp_dtype is the storage type of tp.
 cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStream_t s);
 int cheb_grid(int w);
+
+// One column tile of one graph in a batched filtering launch.
+struct BatchTile {
+  StepArgs a;           // graph and tile pointers; tg/tp/tn/j/part/tp_unscaled set per step
+  void* buf[3];         // rotating n x w blocks; buf[0] holds T_0 (dtype t0_dtype)
+  int t0_dtype;
+  int lpr;              // w / 4
+  int64_t blk0;         // index of this tile's first edge block in the flat item list
+  double* mom;          // [2m+1] trace sums of the graph (E/F rows), float64 atomics
+  uint64_t seed;        // signal stream of the graph
+  int64_t col0;         // global column id of this tile's first column
+  int valid;            // real columns in this tile (the rest are zero padding)
+  float inv_sqrt_d;
+};
+
+// Persistent cooperative launch over all tiles: signals, first step and m-1 steps separated
+// by grid barriers (bounded spin; a timeout sets *err = 1 and every block returns).
+// item_tile[i] = tile of flat edge-block item i (nitems items).
+cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, int64_t nitems,
+                                int m, unsigned int* barrier, int* err, int grid, cudaStream_t s);
+int cheb_batched_grid();
 // Sums partials[(q * nslots + slot) * grid + b] over b (fixed order) into out[q * nslots + slot]
 // for q in 0..nq-1, accumulating across `tiles` consecutive partial blocks of stride tile_stride.
 cudaError_t launch_reduce_partials(const double* part, int nrows, int grid, int tiles,
@@ -158,3 +180,54 @@ csc_status kmeans_run(KmeansState& st, const void* y, int y_dtype, int64_t n, in
 void kmeans_release(KmeansState& st);
 
 }  // namespace csc
+
+// Library context (opaque to callers; see include/csc.h).
+struct csc_ctx {
+  csc_opts opts;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  csc::Graph g;
+  // filtering
+  csc::DevBuf tbuf[3];
+  csc::DevBuf psi;
+  csc::DevBuf part;
+  csc::DevBuf ef;          // reduced E/F sums, double[2m+1]
+  csc::DevBuf coef;        // float[m+1]
+  csc::DevBuf rstage;      // caller signal block staged on the device
+  std::vector<double> mu;
+  int last_m = 0;
+  // feature ring (Eq. 6)
+  int64_t ring_n = 0;
+  int ring_d = 0;
+  csc::DevBuf theta;       // float n x d
+  csc::DevBuf y;           // n x d, float or bf16 (row-normalised features)
+  csc::DevBuf slot_src;    // int[d]
+  std::vector<int64_t> stamp;
+  int64_t t = 0;
+  int64_t next_id = 0;
+  bool has_lambda = false;
+  double lambda = 0.0;
+  // k-means
+  csc::KmeansState km;
+  csc::DevBuf prev_assign;
+  int prev_k = 0;
+  bool has_prev = false;
+  csc::DevBuf ystage;      // caller features staged on the device
+  csc::DevBuf astage;      // caller assignment staged on the device
+  csc::DevBuf out_stage;   // conversions before a host copy
+  csc::DevBuf bad;         // CSR violation counter
+  // counters (csc_get_stats)
+  int64_t launches = 0, step_launches = 0, filter_passes = 0;
+  double step_ms = 0.0;
+  int last_tile = 0;
+  std::vector<cudaEvent_t> events;  // timing event pairs, one per column tile
+  // batched filtering (batched.cu)
+  csc::DevBuf b_prep, b_tbuf, b_psi, b_coef, b_mom, b_tiles, b_items, b_bar, b_tune, b_part;
+  cudaStream_t b_cap = nullptr;
+  cudaGraphExec_t b_exec = nullptr;
+  std::vector<uint64_t> b_sig;              // launch signature of b_exec
+  std::map<uint64_t, int> tune;             // size class -> column tile
+  int64_t batched_launches = 0, graph_replays = 0, autotune_trials = 0;
+};
+

@@ -2,36 +2,13 @@
 //
 // Counter-based so that every (row, global column) entry is addressable on its own:
 // a reused column (Eq. 6) is never regenerated and a refiltered column sees the same
-// signal.  Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011) with counter
-// (row lo, row hi, column, 0) and key (seed lo, seed hi); Box-Muller (1958) on
-// u1 = (x0 >> 8 + 1) 2^-24 in (0, 1] and u2 = (x1 >> 8) 2^-24, both exact in float32.
+// signal (generator in philox.cuh).
 #include "csc_internal.h"
+#include "philox.cuh"
 
 namespace csc {
 
 namespace {
-
-struct U4 { uint32_t x, y, z, w; };
-
-__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) { k0 += W0; k1 += W1; }
-    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-  }
-  return c;
-}
-
-__device__ __forceinline__ float gauss(uint64_t row, uint64_t gcol, uint32_t k0, uint32_t k1) {
-  const U4 x = philox10(U4{(uint32_t)row, (uint32_t)(row >> 32), (uint32_t)gcol, 0u}, k0, k1);
-  const float u1 = ((float)(x.x >> 8) + 1.0f) * 5.9604644775390625e-8f;  // 2^-24
-  const float u2 = (float)(x.y >> 8) * 5.9604644775390625e-8f;
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-}
 
 template <typename T>
 __device__ __forceinline__ T cvt(float v);
@@ -49,7 +26,7 @@ __global__ void signals_kernel(T* __restrict__ out, int64_t n, int w, int64_t ld
     const int64_t row = e / w;
     const int v = (int)(e - row * w);
     float val = 0.0f;
-    if (v < valid) val = gauss((uint64_t)row, (uint64_t)(col0 + v), k0, k1) * inv_sqrt_d;
+    if (v < valid) val = gauss_signal((uint64_t)row, (uint64_t)(col0 + v), k0, k1) * inv_sqrt_d;
     out[row * ld + v] = cvt<T>(val);
   }
 }

@@ -1,0 +1,98 @@
+"""Batched filtering (many graphs, one persistent launch) against per-graph filtering and the oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import chebyshev as cb
+from oracle import laplacian as lp
+from oracle.philox import gaussian_columns
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+BF16_TOL = 3e-3
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _batch(seed=0, count=7):
+    """Uneven graphs: SBM and Chung-Lu, n from 150 to 6000, k from 5 to 20, d = 4k (ragged tiles)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(150), np.log(6000))))
+        k = int(rng.integers(5, 21))
+        deg = float(rng.uniform(8, 30))
+        g = (W.sbm_graph(n, k, deg, 10, seed=100 + i) if i % 2 == 0 else
+             W.chung_lu_graph(n, 2.5, deg, k, 0.2, seed=200 + i))
+        out.append(dict(g=g, c=4 * k, d=4 * k, lam=float(rng.uniform(0.2, 1.2)), seed=1000 + i))
+    return out
+
+
+def _descs(batch):
+    descs = []
+    for b in batch:
+        g = b["g"]
+        descs.append(dict(n=g.n, row_ptr=torch.from_numpy(g.row_ptr).cuda(),
+                          col_idx=torch.from_numpy(g.col_idx).cuda(), vals=None, c=b["c"], d=b["d"],
+                          lambda_c=b["lam"], seed=b["seed"],
+                          psi=torch.zeros((g.n, b["c"]), device="cuda")))
+    return descs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_matches_oracle(gpu_lib, precision):
+    m = 30
+    batch = _batch()
+    descs = _descs(batch)
+    with gpu_lib.Context({"precision": precision}) as ctx:
+        mu = ctx.filter_batched(descs, m)
+        st = ctx.stats()
+    assert st["batched_launches"] == 1 and st["autotune_trials"] >= 1
+    for b, dsc, mu_g in zip(batch, descs, mu):
+        g = b["g"]
+        lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+        r = gaussian_columns(b["seed"], g.n, np.arange(b["c"]), b["d"])
+        if precision == 1:
+            r_used = torch.from_numpy(r.astype(np.float32)).to(torch.bfloat16).double().numpy()
+        else:
+            r_used = r
+        ref = cb.cheb_filter(lt, r_used, m, b["lam"])
+        got = dsc["psi"].cpu().numpy()
+        # float32 signals differ from the float64 draws by float32 rounding (~1e-7)
+        assert rel(got, ref) < FP32_TOL, (g.n, b["c"])
+        if precision == 1:
+            assert rel(got, cb.cheb_filter(lt, r, m, b["lam"])) < BF16_TOL
+        mu_ref = cb.moments(lt, r_used, 2 * m)
+        assert np.max(np.abs(mu_g - mu_ref)) < FP32_TOL * mu_ref[0]
+
+
+def test_batched_replay_and_per_graph_agreement(gpu_lib):
+    m = 25
+    batch = _batch(seed=3, count=5)
+    descs = _descs(batch)
+    with gpu_lib.Context() as ctx:
+        ctx.filter_batched(descs, m)
+        first = [d["psi"].clone() for d in descs]
+        for d in descs:
+            d["psi"].zero_()
+        mu2 = ctx.filter_batched(descs, m)
+        st = ctx.stats()
+        assert st["batched_launches"] == 2
+        for a, d in zip(first, descs):
+            assert torch.equal(a, d["psi"])           # replay reproduces the first run exactly
+        # per-graph path with the same counter-based signals
+        for b, d, mu_g in zip(batch, descs, mu2):
+            g = b["g"]
+            ctx.set_graph(g.n, d["row_ptr"], d["col_idx"])
+            r = torch.zeros((g.n, b["c"]), device="cuda")
+            ctx.signals(b["seed"], g.n, 0, b["c"], b["d"], r)
+            ref = torch.zeros_like(r)
+            mu_ref = ctx.cheb_filter(m, b["lam"], r, ref)
+            assert rel(d["psi"].cpu().numpy(), ref.cpu().numpy()) < FP32_TOL
+            assert np.max(np.abs(mu_g - mu_ref)) < FP32_TOL * mu_ref[0]
