@@ -48,6 +48,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="column-tile width (0 = library default)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
     return a
@@ -198,6 +199,66 @@ def cpu_baseline(graph, seconds_hint=True):
                       f"first snapshot (n={graph.n}, nnz={graph.nnz}), {dt:.1f} s"}
 
 
+def batched_comparison(seed=77, count=128, m=60):
+    """Batched BF16 (one persistent graph-captured launch) vs plain FP32 (one graph at a time)
+    on a batch shaped like the many-graphs workload, scaled down to 128 graphs with n
+    log-uniform in [1e3, 5e4], k ~ U{5..50}, degree ~ U[10, 40], d = 4k, m = 60."""
+    import numpy as np
+    import torch
+
+    import paper_1706_03591_gb300 as csc
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    graphs = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(5e4))))
+        k = int(rng.integers(5, 51))
+        deg = float(rng.uniform(10, 40))
+        g = (W.sbm_graph(n, k, deg, 10, seed=seed + i) if i % 2 == 0 else
+             W.chung_lu_graph(n, 2.5, deg, k, 0.2, seed=seed + i))
+        graphs.append(dict(n=g.n, row_ptr=torch.from_numpy(g.row_ptr).cuda(),
+                           col_idx=torch.from_numpy(g.col_idx).cuda(), vals=None, c=4 * k, d=4 * k,
+                           lambda_c=float(rng.uniform(0.2, 1.0)), seed=seed * 1000 + i,
+                           psi=torch.zeros((g.n, 4 * k), device="cuda")))
+    units = float(sum(g["col_idx"].numel() * g["c"] * m for g in graphs))
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with csc.Context({"precision": 1}) as ctx:
+        ctx.filter_batched(graphs, m)          # plan, autotune, capture
+        ctx.stats(reset=True)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        reps = 3
+        for _ in range(reps):
+            ctx.filter_batched(graphs, m)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        st = ctx.stats()
+    t_batched = ev[0].elapsed_time(ev[1]) / reps
+    with csc.Context({"precision": 0}) as ctx:
+        rbuf = torch.zeros(max(g["n"] * g["c"] for g in graphs), device="cuda")
+        def plain():
+            for g in graphs:
+                ctx.set_graph(g["n"], g["row_ptr"], g["col_idx"])
+                r = rbuf[: g["n"] * g["c"]].view(g["n"], g["c"])
+                ctx.signals(g["seed"], g["n"], 0, g["c"], g["d"], r)
+                ctx.cheb_filter(m, g["lambda_c"], r, g["psi"], want_moments=True)
+        plain()
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        plain()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+    t_plain = ev[2].elapsed_time(ev[3])
+    return {"workload": f"{count} graphs (SBM / Chung-Lu alternating), n log-uniform [1e3, 5e4], "
+                        f"k U[5,50], degree U[10,40], d=4k, m={m}",
+            "graphs": count, "units_per_batch": units,
+            "batched_bf16": {"value": units / (t_batched / 1e3), "ms": t_batched,
+                             "graph_replays": st["graph_replays"], "launches": st["batched_launches"]},
+            "plain_fp32": {"value": units / (t_plain / 1e3), "ms": t_plain},
+            "speedup": t_plain / t_batched, "unit": UNIT}
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return 0
@@ -324,6 +385,11 @@ def run_ours(a, rank, world, local):
     base = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         base = cpu_baseline(snaps[0])
+    batched = None
+    if rank == 0 and not a.no_batched:
+        del dev_graphs
+        torch.cuda.empty_cache()
+        batched = batched_comparison()
     dist.close()
     if rank != 0:
         return 0
@@ -347,6 +413,7 @@ def run_ours(a, rank, world, local):
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": stats["launches"],
+        "batched_vs_plain": batched,
         "phase_ms": phases,
         "per_step": {"lambda": [i["lam"] for i in info], "evals": [i["evals"] for i in info],
                      "kmeans_iters": [i["iters"] for i in info]},
