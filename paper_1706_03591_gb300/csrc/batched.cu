@@ -65,6 +65,7 @@ struct GraphPlan {
   size_t off_scale, off_vs, off_ivs, off_deg, off_blk;  // in b_prep
   size_t off_psi;                                        // in b_psi (floats)
   int w, ntiles, cpad, nblk;
+  int64_t units;
 };
 
 }  // namespace
@@ -183,7 +184,9 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     p.off_psi = psi_floats;
     psi_floats += (size_t)descs[g].n * p.cpad;
     tbuf_floats += (size_t)3 * descs[g].n * p.cpad;
-    nitems += (int64_t)p.ntiles * p.nblk;
+    p.units = std::max<int64_t>(p.nblk, (descs[g].n + csc::step_block_rows(p.w / 4) - 1) /
+                                           csc::step_block_rows(p.w / 4));
+    nitems += (int64_t)p.ntiles * p.units;
     total_tiles += p.ntiles;
   }
   if (nitems > INT32_MAX) return fail(ctx, CSC_EINVAL, "csc_filter_batched: batch too large");
@@ -238,7 +241,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
       bt.valid = std::min(p.w, d.c - t * p.w);
       bt.inv_sqrt_d = (float)(1.0 / std::sqrt((double)d.d));
       const int ti = (int)tiles_h.size();
-      for (int b = 0; b < p.nblk; ++b) items_h[(size_t)item++] = ti;
+      for (int64_t b = 0; b < p.units; ++b) items_h[(size_t)item++] = ti;
       tiles_h.push_back(bt);
     }
   }

@@ -46,6 +46,39 @@ __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
 }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
+// L2 eviction priorities: rows gathered from T_j are kept (evict_last) against the streams
+// that pass through once per step (T_{j-1}, Psi), which are marked evict_first.
+__device__ __forceinline__ uint64_t l2_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld4h(const float* ptr, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float4 ld4h(const __nv_bfloat16* ptr, uint64_t pol) {
+  uint32_t x, y;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(x), "=r"(y)
+               : "l"(ptr), "l"(pol));
+  const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x));
+  const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&y));
+  return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+__device__ __forceinline__ void st4h(float* ptr, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ void fma4(float4& acc, float s, float4 v) {
   acc.x = fmaf(s, v.x, acc.x);
   acc.y = fmaf(s, v.y, acc.y);
@@ -109,6 +142,54 @@ __device__ __forceinline__ bool stage_block(const StepArgs& a, Stage& st, int b,
       if (e < ne) {
         st.col[e] = c[u];
         if (need_w) st.wt[e] = v[u];
+      }
+    }
+  }
+  return true;
+}
+
+// Row-based blocks of the general step: a CTA processes kStepPasses full passes of its
+// row-slots per block, so no pass runs half empty; the block's columns are staged here.
+constexpr int kStepEdgeBuf = 5632;  // keeps StageRows under the 48 KB static limit
+constexpr int kStepPasses = 2;
+constexpr int kStepMaxRows = 128;
+struct StageRows {
+  int col[kStepEdgeBuf];
+  float wt[kStepEdgeBuf];
+  int rp[kStepMaxRows + 1];
+};
+
+template <int LPR>
+__host__ __device__ constexpr int step_rows() {
+  return (kBlock / 32) * (32 / LPR) * kStepPasses > kStepMaxRows ? kStepMaxRows
+                                                                 : (kBlock / 32) * (32 / LPR) * kStepPasses;
+}
+
+// Stages rows [rs, re): row offsets, columns (and weights when the graph is weighted).
+// Returns false when the edges exceed the buffer (the block then reads global memory).
+__device__ __forceinline__ bool stage_rows(const StepArgs& a, StageRows& st, int rs, int re) {
+  const int64_t es = __ldg(a.row_ptr + rs);
+  const int64_t ee = __ldg(a.row_ptr + re);
+  if (ee - es > kStepEdgeBuf) return false;
+  for (int i = threadIdx.x; i <= re - rs; i += blockDim.x)
+    st.rp[i] = (int)(__ldcs(a.row_ptr + rs + i) - es);
+  const int ne = (int)(ee - es);
+  const bool weighted = a.val != nullptr;
+  for (int base = 0; base < ne; base += kStageUnroll * blockDim.x) {
+    int c[kStageUnroll];
+    float v[kStageUnroll];
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int e = base + u * blockDim.x + threadIdx.x;
+      c[u] = e < ne ? __ldcs(a.col + es + e) : 0;
+      v[u] = (e < ne && weighted) ? __ldcs(a.val + es + e) : 1.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int e = base + u * blockDim.x + threadIdx.x;
+      if (e < ne) {
+        st.col[e] = c[u];
+        if (weighted) st.wt[e] = v[u];
       }
     }
   }
@@ -240,7 +321,7 @@ __global__ void __launch_bounds__(kBlock) cheb_first_kernel(StepArgs a) {
 constexpr int kRowUnroll = 8;
 
 template <int LPR>
-__device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const Stage& st, bool staged,
+__device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const StageRows& st, bool staged,
                                                  const float* __restrict__ tg, int64_t row, int rl,
                                                  bool valid, int sub) {
   const int w = a.w;
@@ -250,12 +331,13 @@ __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const Stage&
   if (staged) {
     const int beg = st.rp[rl], end = st.rp[rl + 1];
     const bool weighted = a.val != nullptr;
+    const uint64_t keep = l2_keep();
     for (int e0 = beg; e0 < end; e0 += kRowUnroll) {
       float4 v[kRowUnroll];
 #pragma unroll
       for (int u = 0; u < kRowUnroll; ++u) {
         const int e = e0 + u;
-        v[u] = e < end ? ld4(base + (int64_t)st.col[e] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = e < end ? ld4h(base + (int64_t)st.col[e] * w, keep) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       if (weighted) {
 #pragma unroll
@@ -283,7 +365,7 @@ __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const Stage&
 // V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1}, Psi += a_{j+1} T_{j+1}; partials
 // <T_{j+1},T_{j+1}>, <T_{j+1},T_j> accumulated into acc (first lane of each slot).
 template <int LPR, typename TP>
-__device__ __forceinline__ void step_block(const StepArgs& a, Stage& st, int b, double (&acc)[2]) {
+__device__ __forceinline__ void step_block(const StepArgs& a, StageRows& st, int b, double (&acc)[2]) {
   constexpr int S = 32 / LPR;
   constexpr int kRowsPerPass = (kBlock / 32) * S;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -292,9 +374,10 @@ __device__ __forceinline__ void step_block(const StepArgs& a, Stage& st, int b, 
   const TP* __restrict__ tp = static_cast<const TP*>(a.tp);
   const int w = a.w;
   const float aj = a.psi != nullptr ? __ldg(a.coef + a.j + 1) : 0.f;
-  int rs, re;
+  const int rs = b * step_rows<LPR>();
+  const int re = (int)min((int64_t)rs + step_rows<LPR>(), a.n);
   __syncthreads();
-  const bool staged = stage_block<false>(a, st, b, rs, re);
+  const bool staged = stage_rows(a, st, rs, re);
   __syncthreads();
   for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
     const int r = r0 + wid * S + slot;
@@ -303,12 +386,13 @@ __device__ __forceinline__ void step_block(const StepArgs& a, Stage& st, int b, 
     // own-row operands are independent of the gather: issue them first
     float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), own = prev, p = prev;
     float vsi = 1.f, ivsi = 1.f;
+    const uint64_t stream = l2_stream();
     if (valid) {
       vsi = __ldg(a.vs + row);
       ivsi = __ldg(a.ivs + row);
-      prev = ld4(tp + row * w + sub * 4);
-      own = ld4(tg + row * w + sub * 4);
-      if (a.psi != nullptr) p = ld4(a.psi + row * a.ldp + sub * 4);
+      prev = ld4h(tp + row * w + sub * 4, stream);
+      own = ld4h(tg + row * w + sub * 4, l2_keep());
+      if (a.psi != nullptr) p = ld4h(a.psi + row * a.ldp + sub * 4, stream);
     }
     const float4 g = gather_own_row<LPR>(a, st, staged, tg, row, r - rs, valid, sub);
     float e = 0.f, f = 0.f;
@@ -328,7 +412,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, Stage& st, int b, 
         p.y = fmaf(aj, t.y, p.y);
         p.z = fmaf(aj, t.z, p.z);
         p.w = fmaf(aj, t.w, p.w);
-        st4(a.psi + row * a.ldp + sub * 4, p);
+        st4h(a.psi + row * a.ldp + sub * 4, p, stream);
       }
       e = dot4(t, t);
       f = dot4(t, tc);
@@ -347,9 +431,10 @@ __device__ __forceinline__ void step_block(const StepArgs& a, Stage& st, int b, 
 
 template <int LPR, typename TP>
 __global__ void __launch_bounds__(kBlock, 3) cheb_step_kernel(StepArgs a) {
-  __shared__ Stage st;
+  __shared__ StageRows st;
   double acc[2] = {0.0, 0.0};  // <T_{j+1},T_{j+1}>, <T_{j+1},T_j>
-  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) step_block<LPR, TP>(a, st, b, acc);
+  const int nb = (int)((a.n + step_rows<LPR>() - 1) / step_rows<LPR>());
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) step_block<LPR, TP>(a, st, b, acc);
   // every lane may hold a partial: reduce the warp first
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -414,6 +499,7 @@ __device__ __forceinline__ void block_atomic(double (&acc)[NQ], double* dst) {
 
 template <int LPR>
 __device__ void batched_signals(const BatchTile& t, int b) {
+  if (b >= t.a.nblk) return;
   const int rs = __ldg(t.a.blk_row + b), re = __ldg(t.a.blk_row + b + 1);
   const int w = t.a.w;
   const uint32_t k0 = (uint32_t)t.seed, k1 = (uint32_t)(t.seed >> 32);
@@ -429,19 +515,26 @@ __device__ void batched_signals(const BatchTile& t, int b) {
   }
 }
 
+union BatchSmem {
+  Stage e;       // edge-block staging (signals, first step)
+  StageRows r;   // row-block staging (general steps)
+};
+
 template <int LPR>
-__device__ void batched_item(const BatchTile& t, Stage& st, int b, int s) {
+__device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
   StepArgs a = t.a;
   if (s == 1) {
+    if (b >= a.nblk) return;
     a.tg = t.buf[0];
     a.tn = static_cast<float*>(t.buf[1]);
     a.j = 0;
     double acc[3] = {0.0, 0.0, 0.0};
-    if (t.t0_dtype == CSC_BF16) first_block<LPR, __nv_bfloat16>(a, st, b, acc);
-    else first_block<LPR, float>(a, st, b, acc);
+    if (t.t0_dtype == CSC_BF16) first_block<LPR, __nv_bfloat16>(a, sm.e, b, acc);
+    else first_block<LPR, float>(a, sm.e, b, acc);
     // first-step rows of the E/F table: E0, E1, F1
     block_atomic<3>(acc, t.mom);
   } else {
+    if (b >= (int)((a.n + step_rows<LPR>() - 1) / step_rows<LPR>())) return;
     const int j = s - 1;  // produces T_{j+1}
     a.tg = t.buf[j % 3];
     a.tp = t.buf[(j - 1) % 3];
@@ -449,8 +542,8 @@ __device__ void batched_item(const BatchTile& t, Stage& st, int b, int s) {
     a.j = j;
     a.tp_unscaled = j == 1;
     double acc[2] = {0.0, 0.0};
-    if (j == 1 && t.t0_dtype == CSC_BF16) step_block<LPR, __nv_bfloat16>(a, st, b, acc);
-    else step_block<LPR, float>(a, st, b, acc);
+    if (j == 1 && t.t0_dtype == CSC_BF16) step_block<LPR, __nv_bfloat16>(a, sm.r, b, acc);
+    else step_block<LPR, float>(a, sm.r, b, acc);
     block_atomic<2>(acc, t.mom + 2 * (j + 1) - 1);
   }
 }
@@ -459,7 +552,7 @@ __global__ void __launch_bounds__(kBlock, 2) cheb_batched_kernel(const BatchTile
                                                                  const int32_t* __restrict__ item_tile,
                                                                  int64_t nitems, int m,
                                                                  unsigned int* bar, int* err) {
-  __shared__ Stage st;
+  __shared__ BatchSmem st;
   for (int s = 0; s <= m; ++s) {
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
       const int ti = __ldg(item_tile + it);
@@ -561,6 +654,16 @@ cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStre
   const void* fn = tp_dtype == CSC_BF16 ? step_kernel_for<__nv_bfloat16>(lpr)
                                         : step_kernel_for<float>(lpr);
   return launch_any(fn, a, grid, s);
+}
+
+int step_block_rows(int lpr) {
+  switch (lpr) {
+    case 2: return step_rows<2>();
+    case 4: return step_rows<4>();
+    case 8: return step_rows<8>();
+    case 16: return step_rows<16>();
+    default: return step_rows<32>();
+  }
 }
 
 int cheb_batched_grid() {

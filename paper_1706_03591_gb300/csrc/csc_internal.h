@@ -116,7 +116,8 @@ struct BatchTile {
   void* buf[3];         // rotating n x w blocks; buf[0] holds T_0 (dtype t0_dtype)
   int t0_dtype;
   int lpr;              // w / 4
-  int64_t blk0;         // index of this tile's first edge block in the flat item list
+  int64_t blk0;         // index of this tile's first work unit in the flat item list
+                        // (units: max of its edge blocks and its row blocks)
   double* mom;          // [2m+1] trace sums of the graph (E/F rows), float64 atomics
   uint64_t seed;        // signal stream of the graph
   int64_t col0;         // global column id of this tile's first column
@@ -130,6 +131,8 @@ struct BatchTile {
 cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, int64_t nitems,
                                 int m, unsigned int* barrier, int* err, int grid, cudaStream_t s);
 int cheb_batched_grid();
+// Rows per block of the general step kernel for a tile of 4*lpr columns.
+int step_block_rows(int lpr);
 // Sums partials[(q * nslots + slot) * grid + b] over b (fixed order) into out[q * nslots + slot]
 // for q in 0..nq-1, accumulating across `tiles` consecutive partial blocks of stride tile_stride.
 cudaError_t launch_reduce_partials(const double* part, int nrows, int grid, int tiles,
