@@ -254,7 +254,8 @@ def batched_comparison(seed=77, count=128, m=60):
                         f"k U[5,50], degree U[10,40], d=4k, m={m}",
             "graphs": count, "units_per_batch": units,
             "batched_bf16": {"value": units / (t_batched / 1e3), "ms": t_batched,
-                             "graph_replays": st["graph_replays"], "launches": st["batched_launches"]},
+                             "graph_replays": st["graph_replays"], "launches": st["batched_launches"],
+                             "waves": st["batched_waves"]},
             "plain_fp32": {"value": units / (t_plain / 1e3), "ms": t_plain},
             "speedup": t_plain / t_batched, "unit": UNIT}
 
@@ -417,6 +418,8 @@ def run_ours(a, rank, world, local):
         "phase_ms": phases,
         "per_step": {"lambda": [i["lam"] for i in info], "evals": [i["evals"] for i in info],
                      "kmeans_iters": [i["iters"] for i in info]},
+        "kmeans": {"passes": stats["kmeans_passes"],
+                   "near_ties_per_pass": stats["kmeans_near_ties"] / max(1, stats["kmeans_passes"])},
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 1
+#define CSC_ABI_VERSION 2
 
 typedef struct csc_ctx csc_ctx;
 
@@ -83,6 +83,10 @@ typedef struct csc_stats {
   int64_t batched_launches; /* persistent batched kernel launches (direct or in a graph) */
   int64_t graph_replays;    /* batched launches replayed from a captured CUDA graph */
   int64_t autotune_trials;  /* candidate tile timings run by the batched-path autotuner */
+  int64_t batched_waves;    /* L2-sized waves of the last batched call */
+  int64_t kmeans_passes;    /* k-means assignment passes */
+  int64_t kmeans_near_ties; /* rows whose distance-pass margin was within its error bound and
+                               were re-decided exactly (summed over passes) */
 } csc_stats;
 
 /* ---------------------------------------------------------------- library */

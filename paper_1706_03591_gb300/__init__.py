@@ -103,7 +103,9 @@ def csc_get_stats(h, reset: bool = False) -> dict:
     _check(_lib().csc_get_stats(h, C.byref(st), int(reset)), h, "csc_get_stats")
     return dict(launches=st.launches, step_launches=st.step_launches, step_ms=st.step_ms,
                 filter_passes=st.filter_passes, tile=st.tile, batched_launches=st.batched_launches,
-                graph_replays=st.graph_replays, autotune_trials=st.autotune_trials)
+                graph_replays=st.graph_replays, autotune_trials=st.autotune_trials,
+                batched_waves=st.batched_waves, kmeans_passes=st.kmeans_passes,
+                kmeans_near_ties=st.kmeans_near_ties)
 
 
 def csc_set_graph(h, n: int, row_ptr, col_idx, vals=None) -> None:

@@ -37,6 +37,9 @@ class csc_stats(C.Structure):
         ("batched_launches", C.c_int64),
         ("graph_replays", C.c_int64),
         ("autotune_trials", C.c_int64),
+        ("batched_waves", C.c_int64),
+        ("kmeans_passes", C.c_int64),
+        ("kmeans_near_ties", C.c_int64),
     ]
 
 

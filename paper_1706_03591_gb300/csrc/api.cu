@@ -175,11 +175,12 @@ csc_status fail(csc_ctx* ctx, csc_status s, const std::string& msg) {
 
 int tile_width(const csc_ctx* ctx, int64_t n, int c) {
   if (ctx->opts.col_tile > 0) return ctx->opts.col_tile;
-  // The gather of a row is 4w contiguous bytes: wide rows keep more bytes in flight per
-  // request, which measured faster than L2-sized narrow tiles on the at-scale workload.
-  (void)n;
+  // Narrowest tile that covers c, capped at 64 (fewer launches), then halved while the gathered
+  // block n x w floats exceeds 128 MB: at n = 1e6 a 32-column tile measured fastest per column,
+  // ahead of 64 (L2 misses) and 16 (L2-bound gathers); small graphs keep wide tiles.
   int w = 8;
   while (w < 64 && w < c) w *= 2;
+  while (w > 8 && (double)n * w * 4.0 > 128.0 * (1 << 20)) w /= 2;
   return w;
 }
 
@@ -409,7 +410,8 @@ void csc_destroy(csc_ctx* ctx) {
                     &ctx->coef, &ctx->rstage, &ctx->theta, &ctx->y, &ctx->slot_src,
                     &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad,
                     &ctx->b_prep, &ctx->b_tbuf, &ctx->b_psi, &ctx->b_coef, &ctx->b_mom,
-                    &ctx->b_tiles, &ctx->b_items, &ctx->b_bar, &ctx->b_tune, &ctx->b_part};
+                    &ctx->b_tiles, &ctx->b_items, &ctx->b_bar, &ctx->b_tune, &ctx->b_part,
+                    &ctx->b_waves};
   for (DevBuf* b : bufs) csc::release(*b);
   csc::kmeans_release(ctx->km);
   delete ctx;
@@ -427,9 +429,13 @@ csc_status csc_get_stats(csc_ctx* ctx, csc_stats* out, int reset) {
   out->batched_launches = ctx->batched_launches;
   out->graph_replays = ctx->graph_replays;
   out->autotune_trials = ctx->autotune_trials;
+  out->batched_waves = ctx->batched_waves;
+  out->kmeans_passes = ctx->kmeans_passes;
+  out->kmeans_near_ties = ctx->kmeans_near_ties;
   if (reset) {
     ctx->launches = ctx->step_launches = ctx->filter_passes = 0;
     ctx->batched_launches = ctx->graph_replays = ctx->autotune_trials = 0;
+    ctx->kmeans_passes = ctx->kmeans_near_ties = 0;
     ctx->step_ms = 0.0;
   }
   return CSC_OK;
@@ -760,6 +766,8 @@ csc_status csc_kmeans(csc_ctx* ctx, const void* Y, int y_dtype, int64_t n, int d
   csc_status st = csc::kmeans_run(ctx->km, ydev, y_dtype, n, d, ld, k, init_idx, prev,
                                   max_iter > 0 ? max_iter : ctx->opts.max_iter, s, &res, &ctx->err);
   ctx->launches += res.launches;
+  ctx->kmeans_passes += res.iters;
+  ctx->kmeans_near_ties += res.near_ties;
   if (st != CSC_OK) return st;
   const cudaMemcpyKind kind = assign_where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   CUDA_OK(cudaMemcpyAsync(assign_out, res.assign, (size_t)n * 4, kind, s));
@@ -794,6 +802,8 @@ csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_i
                                   warm ? csc::as<int32_t>(ctx->prev_assign) : nullptr,
                                   ctx->opts.max_iter, s, &res, &ctx->err);
   ctx->launches += res.launches;
+  ctx->kmeans_passes += res.iters;
+  ctx->kmeans_near_ties += res.near_ties;
   if (st != CSC_OK) return st;
   ALLOC_OK(csc::ensure(ctx->prev_assign, (size_t)n * 4));
   CUDA_OK(cudaMemcpyAsync(ctx->prev_assign.ptr, res.assign, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));

@@ -65,7 +65,6 @@ struct GraphPlan {
   size_t off_scale, off_vs, off_ivs, off_deg, off_blk;  // in b_prep
   size_t off_psi;                                        // in b_psi (floats)
   int w, ntiles, cpad, nblk;
-  int64_t units;
 };
 
 }  // namespace
@@ -184,9 +183,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     p.off_psi = psi_floats;
     psi_floats += (size_t)descs[g].n * p.cpad;
     tbuf_floats += (size_t)3 * descs[g].n * p.cpad;
-    p.units = std::max<int64_t>(p.nblk, (descs[g].n + csc::step_block_rows(p.w / 4) - 1) /
-                                           csc::step_block_rows(p.w / 4));
-    nitems += (int64_t)p.ntiles * p.units;
+    nitems += (int64_t)p.ntiles * p.nblk;
     total_tiles += p.ntiles;
   }
   if (nitems > INT32_MAX) return fail(ctx, CSC_EINVAL, "csc_filter_batched: batch too large");
@@ -205,6 +202,14 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   std::vector<double> a(m + 1);
   std::vector<csc::BatchTile> tiles_h;
   std::vector<int32_t> items_h((size_t)nitems);
+  // waves: consecutive tiles whose working set (recursion blocks, Psi, and the CSR of each graph
+  // they touch) stays within kWaveBytes, with at least two items per CTA of the grid
+  const int grid = csc::cheb_batched_grid();
+  constexpr size_t kWaveBytes = size_t(48) << 20;
+  std::vector<int64_t> wave_end;
+  size_t wave_ws = 0;
+  int64_t wave_items = 0;
+  int wave_graph = -1;
   tiles_h.reserve(total_tiles);
   size_t toff = 0;
   int64_t item = 0;
@@ -240,8 +245,19 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
       bt.col0 = (int64_t)t * p.w;
       bt.valid = std::min(p.w, d.c - t * p.w);
       bt.inv_sqrt_d = (float)(1.0 / std::sqrt((double)d.d));
+      const size_t tile_ws = (size_t)d.n * p.w * 16 +
+                             (g != wave_graph ? (size_t)d.nnz * 4 + (size_t)d.n * 20 : 0);
+      if (wave_items > 0 && wave_items >= 2 * grid && wave_ws + tile_ws > kWaveBytes) {
+        wave_end.push_back(item);
+        wave_ws = 0;
+        wave_items = 0;
+        wave_graph = -1;
+      }
+      wave_ws += (size_t)d.n * p.w * 16 + (g != wave_graph ? (size_t)d.nnz * 4 + (size_t)d.n * 20 : 0);
+      wave_graph = g;
+      wave_items += p.nblk;
       const int ti = (int)tiles_h.size();
-      for (int64_t b = 0; b < p.units; ++b) items_h[(size_t)item++] = ti;
+      for (int b = 0; b < p.nblk; ++b) items_h[(size_t)item++] = ti;
       tiles_h.push_back(bt);
     }
   }
@@ -249,16 +265,22 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   B_CUDA(cudaMemcpyAsync(ctx->b_tiles.ptr, tiles_h.data(), tiles_h.size() * sizeof(csc::BatchTile),
                          cudaMemcpyHostToDevice, s));
   B_CUDA(cudaMemcpyAsync(ctx->b_items.ptr, items_h.data(), items_h.size() * 4, cudaMemcpyHostToDevice, s));
+  if (wave_end.empty() || wave_end.back() != nitems) wave_end.push_back(nitems);
+  const int nwaves = (int)wave_end.size();
+  B_ALLOC(csc::ensure(ctx->b_waves, wave_end.size() * 8));
+  B_CUDA(cudaMemcpyAsync(ctx->b_waves.ptr, wave_end.data(), wave_end.size() * 8, cudaMemcpyHostToDevice, s));
+  ctx->batched_waves = nwaves;
 
   // ---- the persistent launch, captured once per plan signature and replayed
-  const int grid = csc::cheb_batched_grid();
   unsigned int* bar = static_cast<unsigned int*>(ctx->b_bar.ptr);
   int* err = reinterpret_cast<int*>(bar + 4);
   const csc::BatchTile* tiles_d = static_cast<const csc::BatchTile*>(ctx->b_tiles.ptr);
   const int32_t* items_d = static_cast<const int32_t*>(ctx->b_items.ptr);
+  const int64_t* waves_d = static_cast<const int64_t*>(ctx->b_waves.ptr);
   const size_t mom_bytes = (size_t)n_graphs * rows * 8;
   const std::vector<uint64_t> sig = {(uint64_t)(uintptr_t)tiles_d, (uint64_t)(uintptr_t)items_d,
                                      (uint64_t)nitems, (uint64_t)m, (uint64_t)grid,
+                                     (uint64_t)(uintptr_t)waves_d, (uint64_t)nwaves,
                                      (uint64_t)(uintptr_t)bar, (uint64_t)(uintptr_t)mbase, mom_bytes};
   bool replayed = false;
   if (ctx->b_exec == nullptr || ctx->b_sig != sig) {
@@ -272,7 +294,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     if (ok) {
       const bool body = cudaMemsetAsync(mbase, 0, mom_bytes, ctx->b_cap) == cudaSuccess &&
                         cudaMemsetAsync(bar, 0, 32, ctx->b_cap) == cudaSuccess &&
-                        csc::launch_cheb_batched(tiles_d, items_d, nitems, m, bar, err, grid,
+                        csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, bar, err, grid,
                                                  ctx->b_cap) == cudaSuccess;
       ok = cudaStreamEndCapture(ctx->b_cap, &graph) == cudaSuccess && body && graph != nullptr;
     }
@@ -292,7 +314,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   } else {
     B_CUDA(cudaMemsetAsync(mbase, 0, mom_bytes, s));
     B_CUDA(cudaMemsetAsync(bar, 0, 32, s));
-    B_CUDA(csc::launch_cheb_batched(tiles_d, items_d, nitems, m, bar, err, grid, s));
+    B_CUDA(csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, bar, err, grid, s));
   }
   ctx->batched_launches += 1;
   ctx->graph_replays += replayed ? 1 : 0;

@@ -24,6 +24,8 @@
 // operands (T_{j-1}, T_j, Psi) are loaded before the gather; the slot-0 lanes run the
 // epilogue (recursion, Psi update, dot products).  CTAs stride over the blocks of a grid
 // sized to fill every SM.
+#include <type_traits>
+
 #include "csc_internal.h"
 #include "philox.cuh"
 
@@ -148,22 +150,17 @@ __device__ __forceinline__ bool stage_block(const StepArgs& a, Stage& st, int b,
   return true;
 }
 
-// Row-based blocks of the general step: a CTA processes kStepPasses full passes of its
-// row-slots per block, so no pass runs half empty; the block's columns are staged here.
+// Row-based blocks of the general step: a CTA processes whole passes of its row slots per
+// block, at most kStepRows rows (the staging barriers then come once per 128 rows on large
+// graphs), fewer on small graphs so that every CTA of the grid gets about two blocks; the
+// block's columns are staged here.
 constexpr int kStepEdgeBuf = 5632;  // keeps StageRows under the 48 KB static limit
-constexpr int kStepPasses = 2;
-constexpr int kStepMaxRows = 128;
+constexpr int kStepRows = 128;
 struct StageRows {
   int col[kStepEdgeBuf];
   float wt[kStepEdgeBuf];
-  int rp[kStepMaxRows + 1];
+  int rp[kStepRows + 1];
 };
-
-template <int LPR>
-__host__ __device__ constexpr int step_rows() {
-  return (kBlock / 32) * (32 / LPR) * kStepPasses > kStepMaxRows ? kStepMaxRows
-                                                                 : (kBlock / 32) * (32 / LPR) * kStepPasses;
-}
 
 // Stages rows [rs, re): row offsets, columns (and weights when the graph is weighted).
 // Returns false when the edges exceed the buffer (the block then reads global memory).
@@ -320,8 +317,8 @@ __global__ void __launch_bounds__(kBlock) cheb_first_kernel(StepArgs a) {
 // one row; kRowUnroll predicated 16-byte loads per lane are in flight per batch.
 constexpr int kRowUnroll = 8;
 
-template <int LPR>
-__device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const StageRows& st, bool staged,
+template <int LPR, typename ST>
+__device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const ST& st, bool staged,
                                                  const float* __restrict__ tg, int64_t row, int rl,
                                                  bool valid, int sub) {
   const int w = a.w;
@@ -361,11 +358,14 @@ __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const StageR
   return acc;
 }
 
-// One edge block of a general step (row-parallel: the LPR lanes of a slot own a row):
+// One block of a general step (row-parallel: the LPR lanes of a slot own a row):
 // V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1}, Psi += a_{j+1} T_{j+1}; partials
 // <T_{j+1},T_{j+1}>, <T_{j+1},T_j> accumulated into acc (first lane of each slot).
-template <int LPR, typename TP>
-__device__ __forceinline__ void step_block(const StepArgs& a, StageRows& st, int b, double (&acc)[2]) {
+// ST = StageRows: block b is rows [b R, b R + R) with R two full passes of row slots (the
+// standalone step kernel); ST = Stage: block b is edge block b (the persistent batched kernel,
+// whose items are edge blocks, fewer and larger per grid-barrier phase).
+template <int LPR, typename TP, typename ST>
+__device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, double (&acc)[2]) {
   constexpr int S = 32 / LPR;
   constexpr int kRowsPerPass = (kBlock / 32) * S;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -374,10 +374,16 @@ __device__ __forceinline__ void step_block(const StepArgs& a, StageRows& st, int
   const TP* __restrict__ tp = static_cast<const TP*>(a.tp);
   const int w = a.w;
   const float aj = a.psi != nullptr ? __ldg(a.coef + a.j + 1) : 0.f;
-  const int rs = b * step_rows<LPR>();
-  const int re = (int)min((int64_t)rs + step_rows<LPR>(), a.n);
+  int rs, re;
+  bool staged;
   __syncthreads();
-  const bool staged = stage_rows(a, st, rs, re);
+  if constexpr (std::is_same<ST, StageRows>::value) {
+    rs = b * a.rpb;
+    re = (int)min((int64_t)rs + a.rpb, a.n);
+    staged = stage_rows(a, st, rs, re);
+  } else {
+    staged = stage_block<false>(a, st, b, rs, re);
+  }
   __syncthreads();
   for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
     const int r = r0 + wid * S + slot;
@@ -430,10 +436,11 @@ __device__ __forceinline__ void step_block(const StepArgs& a, StageRows& st, int
 }
 
 template <int LPR, typename TP>
-__global__ void __launch_bounds__(kBlock, 3) cheb_step_kernel(StepArgs a) {
+// Four CTAs per SM (at most 64 registers per thread) keep more gathers in flight.
+__global__ void __launch_bounds__(kBlock, 4) cheb_step_kernel(StepArgs a) {
   __shared__ StageRows st;
   double acc[2] = {0.0, 0.0};  // <T_{j+1},T_{j+1}>, <T_{j+1},T_j>
-  const int nb = (int)((a.n + step_rows<LPR>() - 1) / step_rows<LPR>());
+  const int nb = (int)((a.n + a.rpb - 1) / a.rpb);
   for (int b = blockIdx.x; b < nb; b += gridDim.x) step_block<LPR, TP>(a, st, b, acc);
   // every lane may hold a partial: reduce the warp first
 #pragma unroll
@@ -515,9 +522,8 @@ __device__ void batched_signals(const BatchTile& t, int b) {
   }
 }
 
-union BatchSmem {
-  Stage e;       // edge-block staging (signals, first step)
-  StageRows r;   // row-block staging (general steps)
+struct BatchSmem {
+  Stage e;  // edge-block staging (every step of the persistent kernel)
 };
 
 template <int LPR>
@@ -534,7 +540,7 @@ __device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
     // first-step rows of the E/F table: E0, E1, F1
     block_atomic<3>(acc, t.mom);
   } else {
-    if (b >= (int)((a.n + step_rows<LPR>() - 1) / step_rows<LPR>())) return;
+    if (b >= a.nblk) return;
     const int j = s - 1;  // produces T_{j+1}
     a.tg = t.buf[j % 3];
     a.tp = t.buf[(j - 1) % 3];
@@ -542,19 +548,25 @@ __device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
     a.j = j;
     a.tp_unscaled = j == 1;
     double acc[2] = {0.0, 0.0};
-    if (j == 1 && t.t0_dtype == CSC_BF16) step_block<LPR, __nv_bfloat16>(a, sm.r, b, acc);
-    else step_block<LPR, float>(a, sm.r, b, acc);
+    if (j == 1 && t.t0_dtype == CSC_BF16) step_block<LPR, __nv_bfloat16>(a, sm.e, b, acc);
+    else step_block<LPR, float>(a, sm.e, b, acc);
     block_atomic<2>(acc, t.mom + 2 * (j + 1) - 1);
   }
 }
 
+// Waves keep the working set of the tiles in flight near the L2 size: every tile of a wave runs
+// all m + 1 steps before the next wave starts.
 __global__ void __launch_bounds__(kBlock, 2) cheb_batched_kernel(const BatchTile* __restrict__ tiles,
                                                                  const int32_t* __restrict__ item_tile,
-                                                                 int64_t nitems, int m,
+                                                                 const int64_t* __restrict__ wave_end,
+                                                                 int nwaves, int m,
                                                                  unsigned int* bar, int* err) {
   __shared__ BatchSmem st;
+  int64_t w0 = 0;
+  for (int wv = 0; wv < nwaves; ++wv) {
+  const int64_t w1 = __ldg(wave_end + wv);
   for (int s = 0; s <= m; ++s) {
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (int64_t it = w0 + blockIdx.x; it < w1; it += gridDim.x) {
       const int ti = __ldg(item_tile + it);
       const BatchTile& t = tiles[ti];
       const int b = (int)(it - t.blk0);
@@ -575,6 +587,8 @@ __global__ void __launch_bounds__(kBlock, 2) cheb_batched_kernel(const BatchTile
       }
     }
     if (!grid_barrier(bar, err)) return;
+  }
+  w0 = w1;
   }
 }
 
@@ -653,17 +667,11 @@ cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStre
   const int lpr = a.w / 4;
   const void* fn = tp_dtype == CSC_BF16 ? step_kernel_for<__nv_bfloat16>(lpr)
                                         : step_kernel_for<float>(lpr);
-  return launch_any(fn, a, grid, s);
-}
-
-int step_block_rows(int lpr) {
-  switch (lpr) {
-    case 2: return step_rows<2>();
-    case 4: return step_rows<4>();
-    case 8: return step_rows<8>();
-    case 16: return step_rows<16>();
-    default: return step_rows<32>();
-  }
+  StepArgs b = a;
+  const int64_t rpp = (kBlock / 32) * (32 / lpr);  // rows per pass of the row slots
+  const int64_t want = (a.n + 2 * (int64_t)grid - 1) / (2 * (int64_t)grid);
+  b.rpb = (int)std::min<int64_t>(kStepRows, std::max<int64_t>(rpp, (want + rpp - 1) / rpp * rpp));
+  return launch_any(fn, b, grid, s);
 }
 
 int cheb_batched_grid() {
@@ -677,10 +685,10 @@ int cheb_batched_grid() {
   return grid;
 }
 
-cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, int64_t nitems,
-                                int m, unsigned int* barrier, int* err, int grid, cudaStream_t s) {
-  void* args[] = {(void*)&tiles, (void*)&item_tile, (void*)&nitems, (void*)&m, (void*)&barrier,
-                  (void*)&err};
+cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, const int64_t* wave_end,
+                                int nwaves, int m, unsigned int* barrier, int* err, int grid, cudaStream_t s) {
+  void* args[] = {(void*)&tiles, (void*)&item_tile, (void*)&wave_end, (void*)&nwaves, (void*)&m,
+                  (void*)&barrier, (void*)&err};
   return cudaLaunchCooperativeKernel((const void*)cheb_batched_kernel, dim3(grid), dim3(kBlock), args,
                                      0, s);
 }

@@ -89,6 +89,7 @@ struct StepArgs {
   const float* ivs;     // 1 / vs
   const int32_t* blk_row;  // edge-block partition (nblk + 1)
   int nblk;
+  int rpb;              // rows per block of the general step (set by launch_cheb_step)
   int tp_unscaled;      // 1: tp holds T_{j-1} (step 2 reads T_0 = R), 0: tp holds V_{j-1}
   const void* tg;       // gathered block T_j (n x w)
   const void* tp;       // T_{j-1} (own rows), unused on the first step
@@ -116,8 +117,7 @@ struct BatchTile {
   void* buf[3];         // rotating n x w blocks; buf[0] holds T_0 (dtype t0_dtype)
   int t0_dtype;
   int lpr;              // w / 4
-  int64_t blk0;         // index of this tile's first work unit in the flat item list
-                        // (units: max of its edge blocks and its row blocks)
+  int64_t blk0;         // index of this tile's first edge block in the flat item list
   double* mom;          // [2m+1] trace sums of the graph (E/F rows), float64 atomics
   uint64_t seed;        // signal stream of the graph
   int64_t col0;         // global column id of this tile's first column
@@ -128,11 +128,12 @@ struct BatchTile {
 // Persistent cooperative launch over all tiles: signals, first step and m-1 steps separated
 // by grid barriers (bounded spin; a timeout sets *err = 1 and every block returns).
 // item_tile[i] = tile of flat edge-block item i (nitems items).
-cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, int64_t nitems,
-                                int m, unsigned int* barrier, int* err, int grid, cudaStream_t s);
+// Persistent cooperative launch over the item list, wave by wave: items [wave_end[w-1],
+// wave_end[w]) run all m + 1 steps (signals, first step, m - 1 general steps), a bounded grid
+// barrier after each step, before the next wave starts.
+cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, const int64_t* wave_end,
+                                int nwaves, int m, unsigned int* barrier, int* err, int grid, cudaStream_t s);
 int cheb_batched_grid();
-// Rows per block of the general step kernel for a tile of 4*lpr columns.
-int step_block_rows(int lpr);
 // Sums partials[(q * nslots + slot) * grid + b] over b (fixed order) into out[q * nslots + slot]
 // for q in 0..nq-1, accumulating across `tiles` consecutive partial blocks of stride tile_stride.
 cudaError_t launch_reduce_partials(const double* part, int nrows, int grid, int tiles,
@@ -164,7 +165,33 @@ struct KmeansState {
   DevBuf counters;              // unsigned long long [4]: moved, flagged, work
   DevBuf inertia_part;          // double [grid + 1]
   DevBuf init_idx;              // int64 [k]
+  DevBuf perm, hist;            // int32 [n] rows bucketed by cluster, int32 [blocks][k]
+  // tensor-core distance pass
+  DevBuf ysplit, ynorm;         // bfloat16 [1 or 2][dp / 64][n][64] (y0, y1), float2 [n] row norms
+  DevBuf csplit, cn2t;          // bfloat16 [2][npad][dp] (c0, c1), float [npad] |c|^2
+  DevBuf masks;                 // uint16 [n][npad / 16] candidate masks of near-tie rows
+  alignas(64) unsigned char tmaps[3][128];  // TMA maps of y0, y1 and (c0, c1)
 };
+
+// Shape of the tensor-core distance pass for (n, k, d, dtype); ok = false when k or d
+// do not fit its shared-memory plan (the bound-pruned pass is used instead).
+struct TcPlan {
+  int npad = 0, dp = 0, nk = 0, stages = 0, has_lo = 0, nv = 16;
+  uint32_t stage_bytes = 0, b_bytes = 0, tmem_cols = 0;
+  size_t smem = 0;
+  float kdot = 0.f;
+  bool ok = false;
+};
+TcPlan kmeans_tc_plan(int64_t n, int k, int d, int y_dtype);
+// Splits the features into bfloat16 y0 (and y1), computes their row norms, max |y_il| (atomicMax into the
+// float bits at maxabs_bits, which the caller zeroes) and the TMA maps (once per call).
+cudaError_t kmeans_tc_prepare(KmeansState& st, const TcPlan& p, const void* y, int y_dtype, int64_t n,
+                              int d, int64_t ldy, unsigned int* maxabs_bits, cudaStream_t s);
+// One assignment pass against the float64 centroids in st.c64: counters[0] moves (recorded in
+// st.moved when track), counters[1] near-tie rows, counters[4] error word (a wait expired).
+cudaError_t kmeans_tc_pass(KmeansState& st, const TcPlan& p, const void* y, int y_dtype, int64_t n, int d,
+                           int64_t ldy, int k, int track, cudaStream_t s);
+void kmeans_tc_release(KmeansState& st);
 
 struct KmeansResult {
   int iters = 0;
@@ -173,6 +200,7 @@ struct KmeansResult {
   double inertia = 0.0;
   int32_t* assign = nullptr;   // device pointer to the final assignment (inside the state)
   int64_t launches = 0;        // kernels launched
+  int64_t near_ties = 0;       // rows re-decided exactly, summed over passes
 };
 
 // Runs Lloyd's iteration on device features y (n x d, leading dimension ldy, dtype).
@@ -227,10 +255,12 @@ struct csc_ctx {
   std::vector<cudaEvent_t> events;  // timing event pairs, one per column tile
   // batched filtering (batched.cu)
   csc::DevBuf b_prep, b_tbuf, b_psi, b_coef, b_mom, b_tiles, b_items, b_bar, b_tune, b_part;
+  csc::DevBuf b_waves;  // int64 [waves]: end of each wave in the item list
   cudaStream_t b_cap = nullptr;
   cudaGraphExec_t b_exec = nullptr;
   std::vector<uint64_t> b_sig;              // launch signature of b_exec
   std::map<uint64_t, int> tune;             // size class -> column tile
-  int64_t batched_launches = 0, graph_replays = 0, autotune_trials = 0;
+  int64_t batched_launches = 0, graph_replays = 0, autotune_trials = 0, batched_waves = 0;
+  int64_t kmeans_passes = 0, kmeans_near_ties = 0;
 };
 

@@ -48,10 +48,20 @@ __global__ void maxabs_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, 
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = e / d;
     const int l = (int)(e - row * d);
-    m = fmaxf(m, fabsf(ldf(y + row * ldy + l)));
+    const float a = fabsf(ldf(y + row * ldy + l));
+    m = a <= 3.0e38f ? fmaxf(m, a) : INFINITY;  // NaN/inf -> inf
   }
   for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Counts labels outside [0, k) (a caller's previous assignment on the device).
+__global__ void label_check_kernel(const int32_t* __restrict__ a, int64_t n, int k,
+                                   unsigned long long* __restrict__ bad) {
+  unsigned long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += (a[i] < 0 || a[i] >= k) ? 1ull : 0ull;
+  if (c) atomicAdd(bad, c);
 }
 
 template <typename TY>
@@ -95,6 +105,103 @@ __global__ void update_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, 
       if (tsum[e] != 0ull) atomicAdd(sums + e, tsum[e]);
     for (int e = threadIdx.x; e < k; e += blockDim.x)
       if (tcnt[e] != 0) atomicAdd(counts + e, tcnt[e]);
+  }
+}
+
+// Fixed-point centroid sums by cluster-sorted rows (d <= 256).  The rows are bucketed by
+// cluster with a counting sort (per-block histograms, a scan, a scatter); each warp then sums a
+// run of consecutive bucketed rows in int64 registers and adds a partial to the global sums only
+// when the cluster changes.  Integer sums, so the result does not depend on the order.
+constexpr int kSortBlock = 256;
+
+// Block b owns rows [b R, b R + R), R = ceil(n / gridDim.x); hist[b][j] = its rows in cluster j.
+__global__ void sort_hist_kernel(const int32_t* __restrict__ assign, int64_t n, int k,
+                                 int* __restrict__ hist) {
+  extern __shared__ int sh_hist[];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) sh_hist[j] = 0;
+  __syncthreads();
+  const int64_t R = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * R, r1 = min(n, r0 + R);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) atomicAdd(sh_hist + assign[r], 1);
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hist[(size_t)blockIdx.x * k + j] = sh_hist[j];
+}
+
+// One block: counts[j] = sum_b hist[b][j]; hist[b][j] becomes the first bucket slot of block b
+// in cluster j (clusters in index order, blocks in order within a cluster).
+__global__ void sort_scan_kernel(int* __restrict__ hist, int nblk, int k, int* __restrict__ counts) {
+  __shared__ int tot[1024];
+  __shared__ int base[1024];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    int t = 0;
+    for (int b = 0; b < nblk; ++b) t += hist[(size_t)b * k + j];
+    tot[j] = t;
+    counts[j] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int j = 0; j < k; ++j) { base[j] = acc; acc += tot[j]; }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    int acc = base[j];
+    for (int b = 0; b < nblk; ++b) {
+      const int h = hist[(size_t)b * k + j];
+      hist[(size_t)b * k + j] = acc;
+      acc += h;
+    }
+  }
+}
+
+__global__ void sort_scatter_kernel(const int32_t* __restrict__ assign, int64_t n, int k,
+                                    const int* __restrict__ hist, int32_t* __restrict__ perm) {
+  extern __shared__ int cursor[];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cursor[j] = hist[(size_t)blockIdx.x * k + j];
+  __syncthreads();
+  const int64_t R = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * R, r1 = min(n, r0 + R);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) perm[atomicAdd(cursor + assign[r], 1)] = (int32_t)r;
+}
+
+// Warp w sums bucketed rows [w C, w C + C); lane owns elements lane + 32 i, i < DW.
+template <typename TY, int DW>
+__global__ void seg_sum_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d,
+                               const int32_t* __restrict__ perm, const int32_t* __restrict__ assign,
+                               float scale, unsigned long long* __restrict__ sums) {
+  constexpr int C = 64;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c0 = warp * C; c0 < n; c0 += nwarps * C) {
+    const int64_t c1 = min(n, c0 + C);
+    long long acc[DW];
+#pragma unroll
+    for (int i = 0; i < DW; ++i) acc[i] = 0;
+    int cur = assign[perm[c0]];
+    for (int64_t p = c0; p < c1; ++p) {
+      const int64_t row = perm[p];
+      const int a = assign[row];
+      if (a != cur) {
+#pragma unroll
+        for (int i = 0; i < DW; ++i) {
+          const int l = lane + 32 * i;
+          if (l < d && acc[i] != 0) atomicAdd(sums + (size_t)cur * d + l, (unsigned long long)acc[i]);
+          acc[i] = 0;
+        }
+        cur = a;
+      }
+#pragma unroll
+      for (int i = 0; i < DW; ++i) {
+        const int l = lane + 32 * i;
+        if (l < d) acc[i] += __float2ll_rn(ldf(y + row * ldy + l) * scale);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < DW; ++i) {
+      const int l = lane + 32 * i;
+      if (l < d && acc[i] != 0) atomicAdd(sums + (size_t)cur * d + l, (unsigned long long)acc[i]);
+    }
   }
 }
 
@@ -789,14 +896,18 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
                      cudaStream_t s, KmeansResult* res, std::string* err) {
   const size_t kd = (size_t)k * d;
   const int sms = num_sms();
+  const int y_dtype = sizeof(TY) == 2 ? CSC_BF16 : CSC_F32;
+  const TcPlan tp = kmeans_tc_plan(n, k, d, y_dtype);
+  const bool use_tc = tp.ok;
   if (!ensure(st.c64, kd * 8) || !ensure(st.c32, kd * 4) || !ensure(st.cn2, (size_t)k * 4) ||
       !ensure(st.cmove, (size_t)k * 4) || !ensure(st.bits, 16) || !ensure(st.sums, kd * 8) ||
       !ensure(st.counts, (size_t)k * 4) || !ensure(st.assign, (size_t)n * 4) ||
-      !ensure(st.ub, (size_t)n * 4) || !ensure(st.lbk, (size_t)n * k * 4) ||
-      !ensure(st.work, (size_t)n * 4) || !ensure(st.flagged, (size_t)n * 4) ||
-      !ensure(st.moved, (size_t)n * 12) || !ensure(st.counters, 64) ||
-      !ensure(st.init_idx, (size_t)k * 8) || !ensure(st.inertia_part, ((size_t)sms * 8 + 1) * 8) ||
-      !ensure(st.vstamp, (size_t)n * 4) || !ensure(st.drift, (size_t)(max_iter + 1) * k * 4)) {
+      !ensure(st.flagged, (size_t)n * 4) || !ensure(st.moved, (size_t)n * 12) ||
+      !ensure(st.counters, 64) || !ensure(st.init_idx, (size_t)k * 8) ||
+      !ensure(st.inertia_part, ((size_t)sms * 8 + 1) * 8) ||
+      (!use_tc && (!ensure(st.ub, (size_t)n * 4) || !ensure(st.lbk, (size_t)n * k * 4) ||
+                   !ensure(st.work, (size_t)n * 4) || !ensure(st.vstamp, (size_t)n * 4) ||
+                   !ensure(st.drift, (size_t)(max_iter + 1) * k * 4)))) {
     if (err) *err = "k-means: device allocation failed";
     return CSC_ENOMEM;
   }
@@ -805,13 +916,30 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   int64_t launches = 0;
   // fixed-point scale from max |y|
   CK(cudaMemsetAsync(st.bits.ptr, 0, 16, s));
-  TRACE("maxabs");
-  maxabs_kernel<TY><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, bits + 2);
-  CK(cudaGetLastError());
+  if (use_tc) {
+    // the bfloat16 split for the tensor-core pass also yields max |y|
+    CK(kmeans_tc_prepare(st, tp, y, y_dtype, n, d, ldy, bits + 2, s));
+  } else {
+    TRACE("maxabs");
+    maxabs_kernel<TY><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, bits + 2);
+    CK(cudaGetLastError());
+  }
   ++launches;
+  CK(cudaMemsetAsync(counters + 5, 0, 8, s));
+  if (prev_assign != nullptr) {
+    label_check_kernel<<<sms * 2, 256, 0, s>>>(prev_assign, n, k, counters + 5);
+    CK(cudaGetLastError());
+    ++launches;
+  }
   unsigned int mbits = 0;
+  unsigned long long bad_labels = 0;
   CK(cudaMemcpyAsync(&mbits, bits + 2, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&bad_labels, counters + 5, 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (bad_labels != 0) {
+    if (err) *err = "k-means: previous assignment has labels outside [0, k)";
+    return CSC_EINVAL;
+  }
   float maxabs;
   std::memcpy(&maxabs, &mbits, 4);
   if (!(maxabs < 1e30f)) {
@@ -833,12 +961,37 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   ++launches;
   const size_t smem = kd * 8 + (size_t)k * 4;
   const bool use_smem = smem <= 220 * 1024;
+  const bool use_sort = d <= 256 && k <= 1024;
+  const int sort_grid = sms * 2;
+  if (use_sort && (!ensure(st.perm, (size_t)n * 4) || !ensure(st.hist, (size_t)sort_grid * k * 4))) {
+    if (err) *err = "k-means: device allocation failed";
+    return CSC_ENOMEM;
+  }
   auto accumulate = [&](const int32_t* asg) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(st.sums.ptr, 0, kd * 8, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(st.counts.ptr, 0, (size_t)k * 4, s);
     if (e != cudaSuccess) return e;
     if (asg == nullptr) return cudaSuccess;
+    if (use_sort) {
+      int* hist = as<int>(st.hist);
+      int32_t* perm = as<int32_t>(st.perm);
+      sort_hist_kernel<<<sort_grid, kSortBlock, (size_t)k * 4, s>>>(asg, n, k, hist);
+      sort_scan_kernel<<<1, 1024, 0, s>>>(hist, sort_grid, k, as<int>(st.counts));
+      sort_scatter_kernel<<<sort_grid, kSortBlock, (size_t)k * 4, s>>>(asg, n, k, hist, perm);
+      const int g = sms * 8;
+      unsigned long long* sums = as<unsigned long long>(st.sums);
+      if (d <= 32)
+        seg_sum_kernel<TY, 1><<<g, 256, 0, s>>>(y, ldy, n, d, perm, asg, scale, sums);
+      else if (d <= 64)
+        seg_sum_kernel<TY, 2><<<g, 256, 0, s>>>(y, ldy, n, d, perm, asg, scale, sums);
+      else if (d <= 128)
+        seg_sum_kernel<TY, 4><<<g, 256, 0, s>>>(y, ldy, n, d, perm, asg, scale, sums);
+      else
+        seg_sum_kernel<TY, 8><<<g, 256, 0, s>>>(y, ldy, n, d, perm, asg, scale, sums);
+      launches += 4;
+      return cudaGetLastError();
+    }
     ++launches;
     if (use_smem) {
       e = cudaFuncSetAttribute(update_kernel<TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -866,6 +1019,50 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   CK(accumulate(prev_assign));
   CK(finalize());
 
+  if (use_tc) {
+    // tensor-core distance pass on every row each pass; near ties decided in float64
+    CK(cudaMemsetAsync(counters + 4, 0, 8, s));
+    int it = 0;
+    bool converged = false;
+    int64_t decided = 0;
+    for (it = 1; it <= max_iter; ++it) {
+      CK(cudaMemsetAsync(counters, 0, 32, s));
+      TRACE("tc pass");
+      CK(kmeans_tc_pass(st, tp, y, y_dtype, n, d, ldy, k, it > 1, s));
+      launches += 3;
+      decided += n;
+      unsigned long long cnt[5] = {0, 0, 0, 0, 0};
+      CK(cudaMemcpyAsync(cnt, counters, 40, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (cnt[4] != 0) {
+        if (err) *err = "k-means: a bounded wait in the tensor-core pass expired (code " +
+                        std::to_string(cnt[4]) + ")";
+        return CSC_ETIMEOUT;
+      }
+      const unsigned long long changed = cnt[0];
+      res->near_ties += (int64_t)cnt[1];
+      if (debug_on()) {
+        fprintf(stderr, "[csc] kmeans tc pass %d: near ties %llu moved %llu\n", it, cnt[1], changed);
+        fflush(stderr);
+      }
+      converged = it > 1 && changed == 0;
+      if (converged || it == max_iter) break;
+      if (it == 1 || changed > (unsigned long long)(n / 16)) {
+        CK(accumulate(as<int32_t>(st.assign)));
+      } else {
+        move_kernel<TY><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, as<int32_t>(st.moved), counters, scale,
+                                                as<unsigned long long>(st.sums), as<int>(st.counts));
+        CK(cudaGetLastError());
+        ++launches;
+      }
+      CK(finalize());
+    }
+    if (it > max_iter) it = max_iter;
+    res->iters = it;
+    res->converged = converged;
+    res->decided = decided;
+  }
+
   int assign_grid = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&assign_grid, assign_kernel<TY>, kAssignBlock, 0);
   assign_grid = std::max(1, assign_grid) * sms;
@@ -877,7 +1074,7 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   int it = 0;
   bool converged = false;
   int64_t decided = 0;
-  for (it = 1; it <= max_iter; ++it) {
+  for (it = 1; it <= max_iter && !use_tc; ++it) {
     CK(cudaMemsetAsync(counters, 0, 32, s));
     int64_t rows = n;
     if (it == 1) {
@@ -930,6 +1127,7 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     CK(cudaMemcpyAsync(cnt, counters, 32, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const unsigned long long changed = cnt[0];
+    res->near_ties += (int64_t)cnt[1];
     if (it > 1) rows = (int64_t)cnt[2];
     if (debug_on()) {
       fprintf(stderr, "[csc] kmeans pass %d: refined %lld flagged %llu moved %llu candidates %llu\n",
@@ -954,7 +1152,12 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     for (int j = 0; j < k; ++j)
       cum[(size_t)it * k + j] = cum[(size_t)(it - 1) * k + j] + (double)move_h[j];
   }
-  if (it > max_iter) it = max_iter;
+  if (!use_tc) {
+    if (it > max_iter) it = max_iter;
+    res->iters = it;
+    res->converged = converged;
+    res->decided = decided;
+  }
   // inertia against the centroids the final assignment was computed with
   const int igrid = sms * 8;
   TRACE("inertia");
@@ -967,12 +1170,9 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   double inertia = 0.0;
   CK(cudaMemcpyAsync(&inertia, as<double>(st.inertia_part) + igrid, 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  res->iters = it;
-  res->converged = converged;
   res->inertia = inertia;
   res->assign = as<int32_t>(st.assign);
   res->launches = launches;
-  res->decided = decided;
   return CSC_OK;
 }
 
@@ -993,6 +1193,9 @@ void kmeans_release(KmeansState& st) {
                    &st.assign, &st.ub, &st.lbk, &st.work, &st.flagged, &st.moved, &st.counters,
                    &st.inertia_part, &st.init_idx, &st.vstamp, &st.drift};
   for (DevBuf* b : all) release(*b);
+  release(st.perm);
+  release(st.hist);
+  kmeans_tc_release(st);
 }
 
 }  // namespace csc

@@ -165,7 +165,10 @@ def _kmeans_case(n, d, k, seed, dtype=np.float32):
     return y.astype(dtype), W.forgy_indices(n, k, seed=seed + 1)
 
 
-@pytest.mark.parametrize("n,d,k", [(20000, 64, 10), (20011, 37, 100), (5000, 256, 100), (777, 8, 3)])
+# (5000, 256, 200) does not fit the tensor-core pass's shared-memory plan and takes the
+# bound-pruned pass; (5000, 1024, 16) runs the tensor-core pass over 16 K chunks.
+@pytest.mark.parametrize("n,d,k", [(20000, 64, 10), (20011, 37, 100), (5000, 256, 100), (777, 8, 3),
+                                   (5000, 256, 200), (5000, 1024, 16)])
 def test_kmeans_exact_assignments(gpu_lib, n, d, k):
     y, idx = _kmeans_case(n, d, k, seed=n + d)
     lab_ref, c_ref, it_ref, conv_ref = km.lloyd(y, km.forgy_centroids(y, idx), max_iter=100)
@@ -197,6 +200,52 @@ def test_kmeans_warm_start_and_bf16(gpu_lib):
         out = ctx.kmeans(yb.cuda(), k, idx, max_iter=100)
     np.testing.assert_array_equal(out["assign"], lab_b)
     assert out["iters"] == it_b
+
+
+def test_full_size_kmeans_update_and_sampled_rows(gpu_lib):
+    """n = 1e6 float32 rows, d = 256, k = 100 (the clustering size of the dynamic workload).
+
+    Runs of 2 and 3 passes from the same Forgy rows: the oracle recomputes the update between
+    them on all rows (the centroids of the 3-pass run are the float64 means of the 2-pass
+    assignment), and the assignment of sampled rows against the centroids each run used."""
+    n, d, k = 1_000_000, 256, 100
+    y, _ = W.clustered_points(n, d, k, seed=11, spread=0.6)
+    idx = W.forgy_indices(n, k, seed=12)
+    yd = dev(y)
+    runs = []
+    for passes in (2, 3):
+        with gpu_lib.Context() as ctx:
+            out = ctx.kmeans(yd, k, idx, max_iter=passes,
+                             assign_out=torch.zeros(n, dtype=torch.int32, device="cuda"))
+        runs.append((out["assign"].cpu().numpy(), out["centroids"], out["iters"]))
+    (la, ca, ia), (lb, cb3, ib) = runs
+    assert (ia, ib) == (2, 3)
+    np.testing.assert_allclose(cb3, km.update(y, la, ca), rtol=0, atol=1e-12)
+    sample = np.random.default_rng(5).choice(n, 20000, replace=False)
+    for lab, c in ((la, ca), (lb, cb3)):
+        ref, _ = km.assign(y[sample], c)
+        np.testing.assert_array_equal(lab[sample], ref)
+
+
+@pytest.mark.parametrize("k", [16, 200])
+def test_kmeans_rejects_bad_inputs(gpu_lib, k):
+    """Non-finite features and (device) previous labels outside [0, k) are argument errors,
+    on the tensor-core path (k = 16) and the bound-pruned path (k = 200)."""
+    y, idx = _kmeans_case(3000, 256, k, seed=9)
+    bad = y.copy()
+    bad[17, 3] = np.nan
+    with gpu_lib.Context() as ctx:
+        with pytest.raises(gpu_lib.CscError) as e:
+            ctx.kmeans(dev(bad), k, idx, max_iter=5)
+        assert e.value.status == 1
+        prev = torch.zeros(3000, dtype=torch.int32, device="cuda")
+        prev[5] = k
+        with pytest.raises(gpu_lib.CscError) as e:
+            ctx.kmeans(dev(y), k, idx, prev_assign=prev, max_iter=5,
+                       assign_out=torch.zeros(3000, dtype=torch.int32, device="cuda"))
+        assert e.value.status == 1
+        out = ctx.kmeans(dev(y), k, idx, max_iter=5)   # the context stays usable
+        assert out["iters"] >= 1
 
 
 def test_kmeans_exact_ties_lowest_index(gpu_lib):
