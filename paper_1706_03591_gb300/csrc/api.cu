@@ -411,7 +411,7 @@ void csc_destroy(csc_ctx* ctx) {
                     &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad,
                     &ctx->b_prep, &ctx->b_tbuf, &ctx->b_psi, &ctx->b_coef, &ctx->b_mom,
                     &ctx->b_tiles, &ctx->b_items, &ctx->b_bar, &ctx->b_tune, &ctx->b_part,
-                    &ctx->b_waves};
+                    &ctx->b_waves, &ctx->b_work};
   for (DevBuf* b : bufs) csc::release(*b);
   csc::kmeans_release(ctx->km);
   delete ctx;

@@ -205,7 +205,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   // waves: consecutive tiles whose working set (recursion blocks, Psi, and the CSR of each graph
   // they touch) stays within kWaveBytes, with at least two items per CTA of the grid
   const int grid = csc::cheb_batched_grid();
-  constexpr size_t kWaveBytes = size_t(48) << 20;
+  constexpr size_t kWaveBytes = size_t(256) << 20;
   std::vector<int64_t> wave_end;
   size_t wave_ws = 0;
   int64_t wave_items = 0;
@@ -268,6 +268,9 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   if (wave_end.empty() || wave_end.back() != nitems) wave_end.push_back(nitems);
   const int nwaves = (int)wave_end.size();
   B_ALLOC(csc::ensure(ctx->b_waves, wave_end.size() * 8));
+  const size_t work_bytes = (size_t)nwaves * (m + 1) * 4;
+  B_ALLOC(csc::ensure(ctx->b_work, work_bytes));
+  unsigned int* work = static_cast<unsigned int*>(ctx->b_work.ptr);
   B_CUDA(cudaMemcpyAsync(ctx->b_waves.ptr, wave_end.data(), wave_end.size() * 8, cudaMemcpyHostToDevice, s));
   ctx->batched_waves = nwaves;
 
@@ -280,7 +283,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   const size_t mom_bytes = (size_t)n_graphs * rows * 8;
   const std::vector<uint64_t> sig = {(uint64_t)(uintptr_t)tiles_d, (uint64_t)(uintptr_t)items_d,
                                      (uint64_t)nitems, (uint64_t)m, (uint64_t)grid,
-                                     (uint64_t)(uintptr_t)waves_d, (uint64_t)nwaves,
+                                     (uint64_t)(uintptr_t)waves_d, (uint64_t)nwaves, (uint64_t)(uintptr_t)work,
                                      (uint64_t)(uintptr_t)bar, (uint64_t)(uintptr_t)mbase, mom_bytes};
   bool replayed = false;
   if (ctx->b_exec == nullptr || ctx->b_sig != sig) {
@@ -294,7 +297,8 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     if (ok) {
       const bool body = cudaMemsetAsync(mbase, 0, mom_bytes, ctx->b_cap) == cudaSuccess &&
                         cudaMemsetAsync(bar, 0, 32, ctx->b_cap) == cudaSuccess &&
-                        csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, bar, err, grid,
+                        cudaMemsetAsync(work, 0, work_bytes, ctx->b_cap) == cudaSuccess &&
+                        csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, work, bar, err, grid,
                                                  ctx->b_cap) == cudaSuccess;
       ok = cudaStreamEndCapture(ctx->b_cap, &graph) == cudaSuccess && body && graph != nullptr;
     }
@@ -314,7 +318,8 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   } else {
     B_CUDA(cudaMemsetAsync(mbase, 0, mom_bytes, s));
     B_CUDA(cudaMemsetAsync(bar, 0, 32, s));
-    B_CUDA(csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, bar, err, grid, s));
+    B_CUDA(cudaMemsetAsync(work, 0, work_bytes, s));
+    B_CUDA(csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, work, bar, err, grid, s));
   }
   ctx->batched_launches += 1;
   ctx->graph_replays += replayed ? 1 : 0;

@@ -556,39 +556,49 @@ __device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
 
 // Waves keep the working set of the tiles in flight near the L2 size: every tile of a wave runs
 // all m + 1 steps before the next wave starts.
+// Items are claimed dynamically (one counter per wave and step) because their cost varies
+// with the tile width of their graph.
 __global__ void __launch_bounds__(kBlock, 2) cheb_batched_kernel(const BatchTile* __restrict__ tiles,
                                                                  const int32_t* __restrict__ item_tile,
                                                                  const int64_t* __restrict__ wave_end,
                                                                  int nwaves, int m,
-                                                                 unsigned int* bar, int* err) {
+                                                                 unsigned int* work, unsigned int* bar,
+                                                                 int* err) {
   __shared__ BatchSmem st;
+  __shared__ int64_t claim;
   int64_t w0 = 0;
   for (int wv = 0; wv < nwaves; ++wv) {
-  const int64_t w1 = __ldg(wave_end + wv);
-  for (int s = 0; s <= m; ++s) {
-    for (int64_t it = w0 + blockIdx.x; it < w1; it += gridDim.x) {
-      const int ti = __ldg(item_tile + it);
-      const BatchTile& t = tiles[ti];
-      const int b = (int)(it - t.blk0);
-      if (s == 0) {
-        switch (t.lpr) {
-          case 2: batched_signals<2>(t, b); break;
-          case 4: batched_signals<4>(t, b); break;
-          case 8: batched_signals<8>(t, b); break;
-          default: batched_signals<16>(t, b); break;
-        }
-      } else {
-        switch (t.lpr) {
-          case 2: batched_item<2>(t, st, b, s); break;
-          case 4: batched_item<4>(t, st, b, s); break;
-          case 8: batched_item<8>(t, st, b, s); break;
-          default: batched_item<16>(t, st, b, s); break;
+    const int64_t w1 = __ldg(wave_end + wv);
+    for (int s = 0; s <= m; ++s) {
+      unsigned int* ctr = work + (size_t)wv * (m + 1) + s;
+      for (;;) {
+        __syncthreads();  // every thread has read the previous claim
+        if (threadIdx.x == 0) claim = w0 + (int64_t)atomicAdd(ctr, 1u);
+        __syncthreads();
+        const int64_t it = claim;
+        if (it >= w1) break;
+        const int ti = __ldg(item_tile + it);
+        const BatchTile& t = tiles[ti];
+        const int b = (int)(it - t.blk0);
+        if (s == 0) {
+          switch (t.lpr) {
+            case 2: batched_signals<2>(t, b); break;
+            case 4: batched_signals<4>(t, b); break;
+            case 8: batched_signals<8>(t, b); break;
+            default: batched_signals<16>(t, b); break;
+          }
+        } else {
+          switch (t.lpr) {
+            case 2: batched_item<2>(t, st, b, s); break;
+            case 4: batched_item<4>(t, st, b, s); break;
+            case 8: batched_item<8>(t, st, b, s); break;
+            default: batched_item<16>(t, st, b, s); break;
+          }
         }
       }
+      if (!grid_barrier(bar, err)) return;
     }
-    if (!grid_barrier(bar, err)) return;
-  }
-  w0 = w1;
+    w0 = w1;
   }
 }
 
@@ -686,9 +696,10 @@ int cheb_batched_grid() {
 }
 
 cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, const int64_t* wave_end,
-                                int nwaves, int m, unsigned int* barrier, int* err, int grid, cudaStream_t s) {
+                                int nwaves, int m, unsigned int* work, unsigned int* barrier, int* err, int grid,
+                                cudaStream_t s) {
   void* args[] = {(void*)&tiles, (void*)&item_tile, (void*)&wave_end, (void*)&nwaves, (void*)&m,
-                  (void*)&barrier, (void*)&err};
+                  (void*)&work, (void*)&barrier, (void*)&err};
   return cudaLaunchCooperativeKernel((const void*)cheb_batched_kernel, dim3(grid), dim3(kBlock), args,
                                      0, s);
 }

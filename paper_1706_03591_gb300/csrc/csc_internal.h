@@ -131,8 +131,10 @@ struct BatchTile {
 // Persistent cooperative launch over the item list, wave by wave: items [wave_end[w-1],
 // wave_end[w]) run all m + 1 steps (signals, first step, m - 1 general steps), a bounded grid
 // barrier after each step, before the next wave starts.
+// work: [nwaves][m + 1] zeroed item counters (claimed dynamically by the CTAs).
 cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, const int64_t* wave_end,
-                                int nwaves, int m, unsigned int* barrier, int* err, int grid, cudaStream_t s);
+                                int nwaves, int m, unsigned int* work, unsigned int* barrier, int* err, int grid,
+                                cudaStream_t s);
 int cheb_batched_grid();
 // Sums partials[(q * nslots + slot) * grid + b] over b (fixed order) into out[q * nslots + slot]
 // for q in 0..nq-1, accumulating across `tiles` consecutive partial blocks of stride tile_stride.
@@ -256,6 +258,7 @@ struct csc_ctx {
   // batched filtering (batched.cu)
   csc::DevBuf b_prep, b_tbuf, b_psi, b_coef, b_mom, b_tiles, b_items, b_bar, b_tune, b_part;
   csc::DevBuf b_waves;  // int64 [waves]: end of each wave in the item list
+  csc::DevBuf b_work;   // uint32 [waves][m + 1]: item counters of the persistent kernel
   cudaStream_t b_cap = nullptr;
   cudaGraphExec_t b_exec = nullptr;
   std::vector<uint64_t> b_sig;              // launch signature of b_exec

@@ -47,6 +47,8 @@ constexpr int kThreads = 192;            // 6 warps
 constexpr uint32_t kChunkA = kTM * 128;  // bytes of one 128 x 64 bfloat16 chunk
 constexpr int kMaxDynSmem = 232448;      // 227 KB
 constexpr int kMaxStages = 8;
+constexpr int kCn2Slots = 256;           // |c|^2 cache in shared memory, +inf past k
+constexpr int kPrefetch = 4;             // tiles of this CTA prefetched into L2 ahead of the loads
 constexpr long long kWaitCycles = 2000000000LL;  // about a second at the SM clock
 
 struct TcArgs {
@@ -118,6 +120,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
           dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
+}
+
+// L2 prefetch of one box (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  for (int j = threadIdx.x; j < a.npad; j += blockDim.x) cn2s[j] = j < a.k ? a.cn2[j] : INFINITY;
+  for (int j = threadIdx.x; j < kCn2Slots; j += blockDim.x) cn2s[j] = j < a.k ? a.cn2[j] : INFINITY;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -278,7 +288,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                       bar(kBFull));
       uint32_t q = 0;
       bool ok = true;
+      // the stage loads of tile t hit L2: its boxes were prefetched kPrefetch tiles earlier
+      for (int64_t tp = blockIdx.x; tp < ntiles && tp < blockIdx.x + (int64_t)kPrefetch * gridDim.x;
+           tp += gridDim.x)
+        for (int kc = 0; kc < a.nk; ++kc) {
+          tma_prefetch_3d(&tm_y0, 0, (int)(tp * kTM), kc);
+          if (a.has_lo) tma_prefetch_3d(&tm_y1, 0, (int)(tp * kTM), kc);
+        }
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int64_t tp = t + (int64_t)kPrefetch * gridDim.x;
+        if (tp < ntiles)
+          for (int kc = 0; kc < a.nk; ++kc) {
+            tma_prefetch_3d(&tm_y0, 0, (int)(tp * kTM), kc);
+            if (a.has_lo) tma_prefetch_3d(&tm_y1, 0, (int)(tp * kTM), kc);
+          }
         for (int kc = 0; kc < a.nk; ++kc) {
           const uint32_t s = q % S, ph = (q / S) & 1u;
           if (!mbar_wait(bar(kEmpty + s), ph ^ 1u)) {
@@ -376,14 +399,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int q = 0; q < 4; ++q) { best[q] = INFINITY; second[q] = INFINITY; bidx[q] = 0; }
       for (int g = 0; g < groups; ++g) {
         tmem_ld<NV>(taddr + (uint32_t)(g * NV), r);
+        // branch-free: cn2s is +inf past k, so padded columns never win
 #pragma unroll
         for (int x = 0; x < NV; ++x) {
           const int j = g * NV + x, q = x & 3;
-          if (j < a.k) {
-            const float f = fmaf(-2.0f, __uint_as_float(r[x]), cn2s[j]);
-            if (f < best[q]) { second[q] = best[q]; best[q] = f; bidx[q] = j; }
-            else if (f < second[q]) second[q] = f;
-          }
+          const float f = fmaf(-2.0f, __uint_as_float(r[x]), cn2s[j]);
+          const bool lt = f < best[q];
+          second[q] = lt ? best[q] : fminf(second[q], f);
+          bidx[q] = lt ? j : bidx[q];
+          best[q] = lt ? f : best[q];
         }
       }
       float bst = best[0], sec = second[0];
@@ -409,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int x = 0; x < 16; ++x) {
               const int j = g * NV + c * 16 + x;
-              if (j < a.k && fmaf(-2.0f, __uint_as_float(r[c * 16 + x]), cn2s[j]) <= thr) bits |= 1u << x;
+              bits |= (fmaf(-2.0f, __uint_as_float(r[c * 16 + x]), cn2s[j]) <= thr ? 1u : 0u) << x;
             }
             const int wi = g * (NV / 16) + c;
             if (flag && wi < words) a.masks[(size_t)slot * words + wi] = (uint16_t)bits;
@@ -664,7 +688,7 @@ TcPlan kmeans_tc_plan(int64_t n, int k, int d, int y_dtype) {
   const int fixed = 1024 + 8 * (2 * kMaxStages + 6) + 16 + 4 * 256;
   const int room = kMaxDynSmem - fixed - (int)p.b_bytes;
   p.stages = room > 0 ? std::min(kMaxStages, room / (int)p.stage_bytes) : 0;
-  p.smem = 1024 + p.b_bytes + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 + 4 * p.npad;
+  p.smem = 1024 + p.b_bytes + (size_t)p.stages * p.stage_bytes + 8 * (2 * p.stages + 6) + 16 + 4 * kCn2Slots;
   p.tmem_cols = 32;
   while (p.tmem_cols < (uint32_t)(2 * p.npad)) p.tmem_cols <<= 1;
   p.nv = 16;
