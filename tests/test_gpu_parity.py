@@ -290,6 +290,42 @@ def test_algorithm1_dynamic_parity_cfg1(gpu_lib, cfg1_graph):
             assert cost == pytest.approx(math.sqrt(h["inertia"]), rel=1e-5)
 
 
+def test_algorithm1_dynamic_bf16_storage(gpu_lib, cfg1_graph):
+    """The same dynamic sequence with bfloat16 signal and feature storage (float32 recursion,
+    float64 moments): features within 3e-3 of the float64-signal oracle, the same cutoffs, and
+    k-means assignments equal to the oracle's Lloyd iteration run on the GPU's own bfloat16
+    features (Forgy at t = 1, warm start from the previous assignment after)."""
+    n, k, d, m, p, seed = 2000, 10, 64, 50, 0.5, 2024
+    graphs = [cfg1_graph]
+    for t in range(5):
+        graphs.append(W.edge_redraw(graphs[-1], 0.01, seed=100 + t))
+    oracle = DynamicCSC(n, k, d, p, m, seed)
+    prev = None
+    with gpu_lib.Context({"precision": 1}) as ctx:
+        assign = torch.zeros(n, dtype=torch.int32, device="cuda")
+        for t, g in enumerate(graphs):
+            idx = W.forgy_indices(n, k, seed=500 + t)
+            oracle.step(g.row_ptr, g.col_idx, init_idx=idx)
+            h = oracle.history[-1]
+            upload_graph(ctx, g)
+            lam, cnt, ev, cols = ctx.filter(m, d, p, seed, k)
+            ctx.cluster(k, seed, idx, assign)
+            assert cols == h["c"]
+            assert lam == h["lam"], (t, lam, h)
+            assert cnt == pytest.approx(h["count"], rel=1e-2)
+            theta = np.zeros((n, d), dtype=np.float32)
+            ctx.get_features(theta)
+            err = rel(theta, oracle.features())
+            assert err < BF16_TOL, (t, err)
+            y = np.zeros((n, d), dtype=np.float32)
+            ctx.get_features(y, normalized=True)  # the bfloat16 values, widened exactly
+            assert np.array_equal(y, torch.from_numpy(y).to(torch.bfloat16).float().numpy())
+            c0 = km.forgy_centroids(y, idx) if prev is None else km.warm_centroids(y, prev, idx)
+            lab, _, _, _ = km.lloyd(y, c0, max_iter=100)
+            np.testing.assert_array_equal(assign.cpu().numpy(), lab)
+            prev = lab
+
+
 def fp32_floor(lt, r, m, lam, ref):
     """Error of a plain float32 evaluation of the same recursion against float64: the
     rounding floor any float32 implementation of the filter meets at this size."""
