@@ -558,7 +558,7 @@ __device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
 // all m + 1 steps before the next wave starts.
 // Items are claimed dynamically (one counter per wave and step) because their cost varies
 // with the tile width of their graph.
-__global__ void __launch_bounds__(kBlock, 2) cheb_batched_kernel(const BatchTile* __restrict__ tiles,
+__global__ void __launch_bounds__(kBlock, 3) cheb_batched_kernel(const BatchTile* __restrict__ tiles,
                                                                  const int32_t* __restrict__ item_tile,
                                                                  const int64_t* __restrict__ wave_end,
                                                                  int nwaves, int m,
