@@ -49,6 +49,7 @@ def args_parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="column-tile width (0 = library default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-grad", action="store_true", help="skip the differentiation timing")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
     return a
@@ -260,6 +261,51 @@ def batched_comparison(seed=77, count=128, m=60):
             "speedup": t_plain / t_batched, "unit": UNIT}
 
 
+def differentiation_timing(seed=4, reps=3):
+    """Forward (with checkpoints every ceil(sqrt m) steps), loss gradient and vector-Jacobian
+    product of the k-means loss of the filtered features, at the differentiation workload's
+    size: SBM n = 2e5, k = 20, degree 25, d = 128, m = 60, unit weights, float32."""
+    import numpy as np
+    import torch
+
+    import paper_1706_03591_gb300 as csc
+    import workloads as W
+    n, k, c, m = 200_000, 20, 128, 60
+    g = W.sbm_graph(n, k, 25, 10, seed=seed)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    r = torch.randn((g.n, c), device="cuda", generator=gen) / float(np.sqrt(c))
+    mu = torch.nn.functional.normalize(torch.randn((k, c), device="cuda", generator=gen), dim=1)
+    assign = torch.randint(0, k, (g.n,), device="cuda", generator=gen, dtype=torch.int32)
+    a = csc.csc_filter_coeffs(m, 0.3)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with csc.Context() as ctx:
+        ctx.set_graph(g.n, torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda())
+        psi = torch.zeros((g.n, c), device="cuda")
+        gpsi = torch.zeros_like(psi)
+        gw = torch.zeros(g.col_idx.size, device="cuda")
+        t = [0.0, 0.0, 0.0]
+        for rep in range(reps + 1):
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            ctx.filter_forward(m, a, r, psi, 0)
+            ev[1].record(stream)
+            ctx.kmeans_loss_grad(psi, mu, assign, gpsi)
+            ev[2].record(stream)
+            ctx.filter_vjp(gpsi, gw)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                for i in range(3):
+                    t[i] += ev[i].elapsed_time(ev[i + 1]) / reps
+    units = float(g.nnz) * c * m
+    return {"workload": f"SBM n={n}, k={k}, degree 25, d={c}, m={m}, unit weights, fp32, "
+                        "checkpoints every 8 steps", "nnz": int(g.nnz),
+            "forward_ms": t[0], "loss_grad_ms": t[1], "vjp_ms": t[2],
+            "backward_over_forward": t[2] / t[0], "forward_rate": units / (t[0] / 1e3),
+            "unit": UNIT}
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return 0
@@ -391,6 +437,10 @@ def run_ours(a, rank, world, local):
         del dev_graphs
         torch.cuda.empty_cache()
         batched = batched_comparison()
+    grad = None
+    if rank == 0 and not a.no_grad:
+        torch.cuda.empty_cache()
+        grad = differentiation_timing()
     dist.close()
     if rank != 0:
         return 0
@@ -415,6 +465,7 @@ def run_ours(a, rank, world, local):
         "clocks": clk,
         "gpu_launches": stats["launches"],
         "batched_vs_plain": batched,
+        "differentiation": grad,
         "phase_ms": phases,
         "per_step": {"lambda": [i["lam"] for i in info], "evals": [i["evals"] for i in info],
                      "kmeans_iters": [i["iters"] for i in info]},

@@ -287,6 +287,38 @@ csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
                                    double lambda_c, const float* R, int c, int64_t ldr,
                                    float* psi_out, int64_t ldp, double* mu_out, void* cuda_stream);
 
+/* ---------------------------------------------------------------- differentiation */
+/* The paper has no derivative; these calls make its filter (Section 2.2 features
+ * Psi = sum_j a_j T_j(L~) R, Section 3.3) a differentiable layer with respect to the
+ * coefficients a_j and the edge weights W (through L~ = -D^-1/2 W D^-1/2, Section 2.1). */
+
+/* Psi = sum_{j=0}^{m} coef[j] T_j(L~) R on the context's graph (its edge weights, unit if
+ * none) for an arbitrary coefficient vector (host double[m+1]) and the caller's signal block R
+ * (device float32, n x c, leading dimension ldr), written to psi_out (device float32, n x c,
+ * leading dimension ldp).  The recursion state at every stride-th step (stride 0: ceil(sqrt m);
+ * 1: every step, no recomputation later) and a copy of R are kept in the context for
+ * csc_filter_vjp.  Errors: CSC_ESTATE without a graph, CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA. */
+csc_status csc_filter_forward(csc_ctx* ctx, int m, const double* coef, const float* R, int c,
+                              int64_t ldr, float* psi_out, int64_t ldp, int stride);
+
+/* Vector-Jacobian product of the last csc_filter_forward: given grad_psi = dloss/dPsi (device
+ * float32, n x c, leading dimension ldg), writes dloss/dcoef to grad_coef (host double[m+1],
+ * may be NULL) and dloss/dw to grad_w (device float32[nnz] in CSR order, the gradient with
+ * respect to the symmetric weight of each edge, equal at its two stored entries; may be NULL).
+ * The graph must be symmetric.  Errors: CSC_ESTATE without a forward pass (or after a new
+ * graph), CSC_EINVAL (bad arguments, asymmetric graph), CSC_ENOMEM, CSC_ECUDA. */
+csc_status csc_filter_vjp(csc_ctx* ctx, const float* grad_psi, int64_t ldg, double* grad_coef,
+                          float* grad_w);
+
+/* Feature-space k-means loss of Eq. 1 with fixed centroids and assignment:
+ * loss = sum_i || psi_i / ||psi_i|| - mu_{assign[i]} ||^2 (a zero row contributes
+ * ||mu_{assign[i]}||^2 and no gradient) and grad_psi = dloss/dPsi.  psi (n x c, ldp), mu
+ * (k x c, contiguous), assign (int32[n]) and grad_psi (n x c, ldg) on the device; *loss_out on
+ * the host.  Errors: CSC_EINVAL (bad arguments, a label outside [0, k)), CSC_ENOMEM, CSC_ECUDA. */
+csc_status csc_kmeans_loss_grad(csc_ctx* ctx, const float* psi, int64_t ldp, int64_t n, int c,
+                                const float* mu, int k, const int32_t* assign, float* grad_psi,
+                                int64_t ldg, double* loss_out);
+
 #ifdef __cplusplus
 }
 #endif

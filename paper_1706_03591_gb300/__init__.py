@@ -21,6 +21,7 @@ __all__ = [
     "csc_lambda_search_moments", "csc_signals", "csc_cheb_filter", "csc_kmeans",
     "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
+    "csc_filter_forward", "csc_filter_vjp", "csc_kmeans_loss_grad", "cheb_filter_layer",
 ]
 
 
@@ -249,6 +250,90 @@ def csc_filter_batched(h, graphs, m: int, want_moments: bool = True):
     return mu
 
 
+def _device_f32(x, kind: str):
+    import torch
+    if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float32 and x.dim() == 2 and
+            (x.numel() <= 1 or x.stride(1) == 1)):
+        raise ValueError(f"{kind}: expected a CUDA float32 matrix with contiguous rows")
+    return C.c_void_p(x.data_ptr()), int(x.stride(0))
+
+
+def csc_filter_forward(h, m: int, coef, R, psi_out, stride: int = 0) -> None:
+    """Psi = sum_j coef[j] T_j(L~) R into psi_out, keeping the recursion checkpoints for
+    csc_filter_vjp (R and psi_out: CUDA float32, n x c)."""
+    a = np.ascontiguousarray(coef, dtype=np.float64)
+    if a.size != m + 1:
+        raise ValueError("coef must have m + 1 entries")
+    r, ldr = _device_f32(R, "R")
+    p, ldp = _device_f32(psi_out, "psi_out")
+    _check(_lib().csc_filter_forward(h, m, a.ctypes.data_as(C.POINTER(C.c_double)), r, int(R.shape[1]), ldr,
+                                     p, ldp, stride), h, "csc_filter_forward")
+
+
+def csc_filter_vjp(h, m: int, grad_psi, grad_w=None) -> np.ndarray:
+    """dloss/dcoef (float64, m + 1) of the last csc_filter_forward (of order m); dloss/dw
+    written to grad_w (CUDA float32, one entry per stored edge) when given."""
+    g, ldg = _device_f32(grad_psi, "grad_psi")
+    gw = None
+    if grad_w is not None:
+        import torch
+        if not (grad_w.is_cuda and grad_w.dtype == torch.float32 and grad_w.is_contiguous()):
+            raise ValueError("grad_w: expected a contiguous CUDA float32 vector")
+        gw = C.c_void_p(grad_w.data_ptr())
+    out = np.zeros(m + 1)
+    _check(_lib().csc_filter_vjp(h, g, ldg, out.ctypes.data_as(C.POINTER(C.c_double)), gw), h, "csc_filter_vjp")
+    return out
+
+
+def csc_kmeans_loss_grad(h, psi, mu, assign, grad_out) -> float:
+    """loss = sum_i ||psi_i/||psi_i|| - mu[assign[i]]||^2 and dloss/dPsi into grad_out
+    (all CUDA tensors: psi, grad_out float32 n x c, mu float32 k x c, assign int32 n)."""
+    import torch
+    p, ldp = _device_f32(psi, "psi")
+    go, ldg = _device_f32(grad_out, "grad_out")
+    mu = mu.contiguous()
+    if not (mu.is_cuda and mu.dtype == torch.float32 and assign.is_cuda and assign.dtype == torch.int32):
+        raise ValueError("mu: CUDA float32 (k x c); assign: CUDA int32")
+    loss = C.c_double()
+    _check(_lib().csc_kmeans_loss_grad(h, p, ldp, int(psi.shape[0]), int(psi.shape[1]), C.c_void_p(mu.data_ptr()),
+                                       int(mu.shape[0]), C.c_void_p(assign.contiguous().data_ptr()), go, ldg,
+                                       C.byref(loss)), h, "csc_kmeans_loss_grad")
+    return loss.value
+
+
+_FILTER_FN = None
+
+
+def cheb_filter_layer(context, n: int, row_ptr, col_idx, weights, coef, R, stride: int = 0):
+    """Differentiable Psi = sum_j coef[j] T_j(L~(weights)) R (torch.autograd): gradients flow to
+    ``coef`` (float64 tensor, m + 1) and ``weights`` (CUDA float32, one per stored edge, the
+    two copies of an edge holding the same value).  The graph of ``context`` is replaced by
+    (row_ptr, col_idx, weights); one forward may be pending per context."""
+    global _FILTER_FN
+    if _FILTER_FN is None:
+        import torch
+
+        class ChebFilterFunction(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, coef_t, w_t, ctx_obj, n_, rp, ci, r_t, stride_):
+                ctx_obj.set_graph(n_, rp, ci, w_t.detach().contiguous())
+                psi = torch.empty((n_, r_t.shape[1]), device=r_t.device, dtype=torch.float32)
+                csc_filter_forward(ctx_obj.h, coef_t.numel() - 1, coef_t.detach().cpu().numpy(), r_t, psi, stride_)
+                fctx.ctx_obj, fctx.nnz, fctx.m = ctx_obj, int(ci.numel()), coef_t.numel() - 1
+                fctx.coef_meta = (coef_t.dtype, coef_t.device)
+                return psi
+
+            @staticmethod
+            def backward(fctx, grad_psi):
+                gw = torch.empty(fctx.nnz, device=grad_psi.device, dtype=torch.float32)
+                gc = csc_filter_vjp(fctx.ctx_obj.h, fctx.m, grad_psi.contiguous(), gw)
+                gct = torch.from_numpy(gc).to(dtype=fctx.coef_meta[0], device=fctx.coef_meta[1])
+                return gct, gw, None, None, None, None, None, None
+
+        _FILTER_FN = ChebFilterFunction
+    return _FILTER_FN.apply(coef, weights, context, n, row_ptr, col_idx, R, stride)
+
+
 def csc_cheb_filter_noalloc(n: int, row_ptr, col_idx, vals, m: int, lambda_c: float, R,
                             psi_out=None, want_moments: bool = True, stream=None):
     """Allocation-free filter of a device signal block R over a device CSR graph (small
@@ -326,6 +411,16 @@ class Context:
 
     def cluster(self, k, seed, init_idx, assign_out):
         return csc_cluster(self.h, k, seed, init_idx, assign_out)
+
+    def filter_forward(self, m, coef, R, psi_out, stride=0):
+        csc_filter_forward(self.h, m, coef, R, psi_out, stride)
+        self._grad_m = m
+
+    def filter_vjp(self, grad_psi, grad_w=None):
+        return csc_filter_vjp(self.h, getattr(self, "_grad_m", 0), grad_psi, grad_w)
+
+    def kmeans_loss_grad(self, psi, mu, assign, grad_out):
+        return csc_kmeans_loss_grad(self.h, psi, mu, assign, grad_out)
 
     @property
     def last_error(self):

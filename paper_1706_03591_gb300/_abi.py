@@ -89,6 +89,9 @@ SIGNATURES = {
     "csc_filter_batched": (_i32, [_p, _i32, _p, _i32, _pd]),
     "csc_cheb_filter_noalloc": (_i32, [_i64, _i64, _p, _p, _p, _i32, _dbl, _p, _i32, _i64, _p, _i64,
                                        _pd, _p]),
+    "csc_filter_forward": (_i32, [_p, _i32, _pd, _p, _i32, _i64, _p, _i64, _i32]),
+    "csc_filter_vjp": (_i32, [_p, _p, _i64, _pd, _p]),
+    "csc_kmeans_loss_grad": (_i32, [_p, _p, _i64, _i64, _i32, _p, _i32, _p, _p, _i64, _pd]),
 }
 
 _lib = None

@@ -411,7 +411,10 @@ void csc_destroy(csc_ctx* ctx) {
                     &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad,
                     &ctx->b_prep, &ctx->b_tbuf, &ctx->b_psi, &ctx->b_coef, &ctx->b_mom,
                     &ctx->b_tiles, &ctx->b_items, &ctx->b_bar, &ctx->b_tune, &ctx->b_part,
-                    &ctx->b_waves, &ctx->b_work};
+                    &ctx->b_waves, &ctx->b_work,
+                    &ctx->gs.coef_f, &ctx->gs.ckpt, &ctx->gs.seg, &ctx->gs.rt, &ctx->gs.gt,
+                    &ctx->gs.phi[0], &ctx->gs.phi[1], &ctx->gs.phi[2], &ctx->gs.H, &ctx->gs.tpos,
+                    &ctx->gs.nsum, &ctx->gs.part, &ctx->gs.flag, &ctx->gs.ga, &ctx->gs.rcopy};
   for (DevBuf* b : bufs) csc::release(*b);
   csc::kmeans_release(ctx->km);
   delete ctx;
@@ -492,6 +495,8 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
   CUDA_OK(csc::launch_block_rows(g, s));
   ctx->launches += 2;
   g.loaded = true;
+  ctx->graph_version += 1;
+  ctx->gs.ready = false;
   return CSC_OK;
 }
 

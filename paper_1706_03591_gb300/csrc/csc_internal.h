@@ -152,6 +152,31 @@ cudaError_t launch_assemble(float* theta, int64_t ldt, const float* psi, int64_t
 cudaError_t launch_convert(const void* src, int src_dtype, int64_t ld_src, void* dst,
                            int dst_dtype, int64_t ld_dst, int64_t n, int d, cudaStream_t s);
 
+// ------------------------------------------------------------------ differentiation (grad.cu)
+
+// State kept by csc_filter_forward for csc_filter_vjp.
+struct GradState {
+  bool ready = false;
+  int m = 0, c = 0, w = 0, ntiles = 0, stride = 1, segs = 1;
+  const float* R = nullptr;   // the context's copy of the signal block (n x c)
+  int64_t ldr = 0;
+  DevBuf rcopy;
+  std::vector<double> coef;   // a_0 .. a_m
+  DevBuf coef_f;              // float[m + 1]
+  DevBuf ckpt;                // float [ntiles][slots][n][w]: V_j at the segment boundaries
+  int slots = 0;              // checkpoint blocks per tile
+  DevBuf seg;                 // float [stride + 2][n][w]: one recomputed segment
+  DevBuf rt, gt;              // float [n][w]: tile of R, tile of dloss/dPsi
+  DevBuf phi[3];              // float [n][w]: adjoint iterates Phi_j = D^-1/2 Lambda_j
+  DevBuf H;                   // float [nnz]: sum_j c_j <Phi_{j+1}[u], V_j[v]> per stored entry
+  DevBuf tpos;                // int32 [nnz]: position of the transposed entry
+  DevBuf nsum;                // double [n]: per-node sums of the weight chain
+  DevBuf part;                // double block partials of <dloss/dPsi, T_j>
+  DevBuf ga;                  // double [m + 1][ntiles]: per-tile <dloss/dPsi, T_j R>
+  DevBuf flag;                // int64: entries without a transposed partner
+  int64_t graph_version = -1; // graph the transpose map was built for
+};
+
 // ------------------------------------------------------------------ k-means (kmeans.cu)
 
 struct KmeansState {
@@ -221,6 +246,7 @@ struct csc_ctx {
   int device = 0;
   std::string err;
   csc::Graph g;
+  int64_t graph_version = 0;  // incremented by every csc_set_graph
   // filtering
   csc::DevBuf tbuf[3];
   csc::DevBuf psi;
@@ -258,6 +284,7 @@ struct csc_ctx {
   // batched filtering (batched.cu)
   csc::DevBuf b_prep, b_tbuf, b_psi, b_coef, b_mom, b_tiles, b_items, b_bar, b_tune, b_part;
   csc::DevBuf b_waves;  // int64 [waves]: end of each wave in the item list
+  csc::GradState gs;    // differentiation: checkpoints of the last csc_filter_forward
   csc::DevBuf b_work;   // uint32 [waves][m + 1]: item counters of the persistent kernel
   cudaStream_t b_cap = nullptr;
   cudaGraphExec_t b_exec = nullptr;
