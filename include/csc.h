@@ -319,6 +319,17 @@ csc_status csc_kmeans_loss_grad(csc_ctx* ctx, const float* psi, int64_t ldp, int
                                 const float* mu, int k, const int32_t* assign, float* grad_psi,
                                 int64_t ldg, double* loss_out);
 
+/* ---------------------------------------------------------------- snapshot similarity */
+
+/* Edge similarity of Definition 4.1: *rho_out = ||L_b - L_a||_F for the normalized
+ * Laplacians L = I - D^-1/2 W D^-1/2 of two graphs a and b on the same n nodes, each a
+ * device CSR (row_ptr int64[n+1], col_idx int32 with strictly increasing columns per row,
+ * vals float32 or NULL for unit weights).  Corollary 4.2 bounds the change of the spectral
+ * projector by sqrt(2)/alpha times rho.  Errors: CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA. */
+csc_status csc_laplacian_distance(csc_ctx* ctx, int64_t n, const int64_t* rp_a, const int32_t* col_a,
+                                  const float* val_a, const int64_t* rp_b, const int32_t* col_b,
+                                  const float* val_b, double* rho_out);
+
 #ifdef __cplusplus
 }
 #endif

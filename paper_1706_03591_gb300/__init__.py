@@ -22,6 +22,7 @@ __all__ = [
     "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
     "csc_filter_forward", "csc_filter_vjp", "csc_kmeans_loss_grad", "cheb_filter_layer",
+    "csc_laplacian_distance",
 ]
 
 
@@ -301,6 +302,18 @@ def csc_kmeans_loss_grad(h, psi, mu, assign, grad_out) -> float:
     return loss.value
 
 
+def csc_laplacian_distance(h, n: int, graph_a, graph_b) -> float:
+    """||L_b - L_a||_F (Definition 4.1); each graph is (row_ptr, col_idx, vals or None) of
+    CUDA tensors."""
+    ptrs = []
+    for rp, ci, vv in (graph_a, graph_b):
+        ptrs += [C.c_void_p(rp.data_ptr()), C.c_void_p(ci.data_ptr()) if ci.numel() else None,
+                 None if vv is None else C.c_void_p(vv.data_ptr())]
+    rho = C.c_double()
+    _check(_lib().csc_laplacian_distance(h, n, *ptrs, C.byref(rho)), h, "csc_laplacian_distance")
+    return rho.value
+
+
 _FILTER_FN = None
 
 
@@ -421,6 +434,9 @@ class Context:
 
     def kmeans_loss_grad(self, psi, mu, assign, grad_out):
         return csc_kmeans_loss_grad(self.h, psi, mu, assign, grad_out)
+
+    def laplacian_distance(self, n, graph_a, graph_b):
+        return csc_laplacian_distance(self.h, n, graph_a, graph_b)
 
     @property
     def last_error(self):

@@ -92,6 +92,7 @@ SIGNATURES = {
     "csc_filter_forward": (_i32, [_p, _i32, _pd, _p, _i32, _i64, _p, _i64, _i32]),
     "csc_filter_vjp": (_i32, [_p, _p, _i64, _pd, _p]),
     "csc_kmeans_loss_grad": (_i32, [_p, _p, _i64, _i64, _i32, _p, _i32, _p, _p, _i64, _pd]),
+    "csc_laplacian_distance": (_i32, [_p, _i64, _p, _p, _p, _p, _p, _p, _pd]),
 }
 
 _lib = None

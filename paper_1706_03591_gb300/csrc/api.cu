@@ -414,7 +414,7 @@ void csc_destroy(csc_ctx* ctx) {
                     &ctx->b_waves, &ctx->b_work,
                     &ctx->gs.coef_f, &ctx->gs.ckpt, &ctx->gs.seg, &ctx->gs.rt, &ctx->gs.gt,
                     &ctx->gs.phi[0], &ctx->gs.phi[1], &ctx->gs.phi[2], &ctx->gs.H, &ctx->gs.tpos,
-                    &ctx->gs.nsum, &ctx->gs.part, &ctx->gs.flag, &ctx->gs.ga, &ctx->gs.rcopy};
+                    &ctx->gs.nsum, &ctx->gs.part, &ctx->gs.flag, &ctx->gs.ga, &ctx->gs.rcopy, &ctx->sim};
   for (DevBuf* b : bufs) csc::release(*b);
   csc::kmeans_release(ctx->km);
   delete ctx;
@@ -451,10 +451,6 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
     return fail(ctx, CSC_EINVAL, "csc_set_graph: bad sizes or pointers");
   if (ctx->t > 0 && n != ctx->ring_n)
     return fail(ctx, CSC_EINVAL, "csc_set_graph: the vertex set is fixed across snapshots");
-  if (where == CSC_HOST) {
-    csc_status st = validate_host_csr(ctx, n, nnz, row_ptr, col_idx, vals);
-    if (st != CSC_OK) return st;
-  }
   cudaStream_t s = ctx->stream;
   csc::Graph& g = ctx->g;
   ALLOC_OK(csc::ensure(g.row_ptr, (size_t)(n + 1) * 8));
@@ -474,7 +470,9 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
   }
   g.n = n;
   g.nnz = nnz;
-  if (where == CSC_DEVICE && ctx->opts.checked) {
+  // host input is always validated, on the device after the upload (an O(nnz) pass on the host
+  // would cost more than the copy); the host validator runs only to name a failure
+  if (where == CSC_HOST || ctx->opts.checked) {
     ALLOC_OK(csc::ensure(ctx->bad, 16));
     CUDA_OK(cudaMemsetAsync(ctx->bad.ptr, 0, 8, s));
     CUDA_OK(csc::launch_graph_check(g, csc::as<unsigned long long>(ctx->bad), s));
@@ -487,6 +485,10 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
     CUDA_OK(cudaStreamSynchronize(s));
     if (bad != 0 || ends[0] != 0 || ends[1] != nnz) {
       g.loaded = false;
+      if (where == CSC_HOST) {
+        csc_status st = validate_host_csr(ctx, n, nnz, row_ptr, col_idx, vals);
+        if (st != CSC_OK) return st;
+      }
       return fail(ctx, CSC_EINVAL, "csc_set_graph: malformed CSR (" + std::to_string(bad) +
                                        " violations)");
     }

@@ -285,6 +285,7 @@ struct csc_ctx {
   csc::DevBuf b_prep, b_tbuf, b_psi, b_coef, b_mom, b_tiles, b_items, b_bar, b_tune, b_part;
   csc::DevBuf b_waves;  // int64 [waves]: end of each wave in the item list
   csc::GradState gs;    // differentiation: checkpoints of the last csc_filter_forward
+  csc::DevBuf sim;      // csc_laplacian_distance scratch: double [2n + 2 grid + 8]
   csc::DevBuf b_work;   // uint32 [waves][m + 1]: item counters of the persistent kernel
   cudaStream_t b_cap = nullptr;
   cudaGraphExec_t b_exec = nullptr;

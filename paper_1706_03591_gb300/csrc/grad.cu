@@ -74,7 +74,7 @@ struct AdjArgs {
 
 // One reverse step: row-parallel, the LPR = w / 4 lanes of a slot own a row.
 template <int LPR>
-__global__ void __launch_bounds__(kBlk) adjoint_step_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(kBlk, 3) adjoint_step_kernel(AdjArgs a) {
   constexpr int S = 32 / LPR;
   const int lane = threadIdx.x & 31;
   const int slot = lane / LPR, sub = lane % LPR;
@@ -121,14 +121,25 @@ __global__ void __launch_bounds__(kBlk) adjoint_step_kernel(AdjArgs a) {
         acc.w = fmaf(wt[u], pv[u].w, acc.w);
         dot[u] = dot4v(p1, vv[u]) * sv[u];
       }
+      // reduce-scatter of the four per-edge dots over the LPR lanes of the slot: the first two
+      // exchanges hand each half of the lanes half of the edges, a butterfly finishes
+      const int hA = LPR / 2;
+      const bool upA = (sub & hA) != 0;
+      float k0 = upA ? dot[2] : dot[0], k1 = upA ? dot[3] : dot[1];
+      k0 += __shfl_xor_sync(kAll, upA ? dot[0] : dot[2], hA);
+      k1 += __shfl_xor_sync(kAll, upA ? dot[1] : dot[3], hA);
+      if constexpr (LPR >= 4) {
+        constexpr int hB = LPR / 4;
+        const bool upB = (sub & hB) != 0;
+        float kk = (upB ? k1 : k0) + __shfl_xor_sync(kAll, upB ? k0 : k1, hB);
 #pragma unroll
-      for (int off = 1; off < LPR; off <<= 1)
-#pragma unroll
-        for (int u = 0; u < kEdgeUnroll; ++u) dot[u] += __shfl_xor_sync(kAll, dot[u], off);
-      if (sub == 0) {
-#pragma unroll
-        for (int u = 0; u < kEdgeUnroll; ++u)
-          if (e0 + u < len) a.H[beg + e0 + u] += a.cj * dot[u];
+        for (int off = hB / 2; off >= 1; off >>= 1) kk += __shfl_xor_sync(kAll, kk, off);
+        const int u = (upA ? 2 : 0) + (upB ? 1 : 0);
+        if (sub % hB == 0 && e0 + u < len) a.H[beg + e0 + u] += a.cj * kk;
+      } else {
+        const int u = upA ? 2 : 0;
+        if (e0 + u < len) a.H[beg + e0 + u] += a.cj * k0;
+        if (e0 + u + 1 < len) a.H[beg + e0 + u + 1] += a.cj * k1;
       }
     }
     // <G, T_j R> over this row's columns: T_j = V_j / vs for j >= 1, R for j == 0
