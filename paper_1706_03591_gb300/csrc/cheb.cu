@@ -329,7 +329,18 @@ __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const ST& st
     const int beg = st.rp[rl], end = st.rp[rl + 1];
     const bool weighted = a.val != nullptr;
     const uint64_t keep = l2_keep();
+    constexpr int kLines = LPR >= 8 ? LPR / 8 : 1;  // 128-byte lines per gathered row
     for (int e0 = beg; e0 < end; e0 += kRowUnroll) {
+      if (a.l2pf) {
+        // the next batch's rows into L2 while this batch loads: more misses in flight without
+        // holding registers (pays off when the gathered block exceeds the L2)
+        for (int q = sub; q < kRowUnroll * kLines; q += LPR) {
+          const int ep = e0 + kRowUnroll + q / kLines;
+          if (ep < end)
+            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(tg + (int64_t)st.col[ep] * w + (q % kLines) * 32)
+                         : "memory");
+        }
+      }
       float4 v[kRowUnroll];
 #pragma unroll
       for (int u = 0; u < kRowUnroll; ++u) {
@@ -681,6 +692,7 @@ cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStre
   const int64_t rpp = (kBlock / 32) * (32 / lpr);  // rows per pass of the row slots
   const int64_t want = (a.n + 2 * (int64_t)grid - 1) / (2 * (int64_t)grid);
   b.rpb = (int)std::min<int64_t>(kStepRows, std::max<int64_t>(rpp, (want + rpp - 1) / rpp * rpp));
+  b.l2pf = (double)a.n * a.w * 4.0 > 64.0 * (1 << 20);
   return launch_any(fn, b, grid, s);
 }
 

@@ -90,6 +90,7 @@ struct StepArgs {
   const int32_t* blk_row;  // edge-block partition (nblk + 1)
   int nblk;
   int rpb;              // rows per block of the general step (set by launch_cheb_step)
+  int l2pf;             // prefetch the next batch of gathered rows into L2 (set by launch_cheb_step)
   int tp_unscaled;      // 1: tp holds T_{j-1} (step 2 reads T_0 = R), 0: tp holds V_{j-1}
   const void* tg;       // gathered block T_j (n x w)
   const void* tp;       // T_{j-1} (own rows), unused on the first step
