@@ -3,7 +3,7 @@
 // Small graphs are launch-bound when filtered one at a time (m launches of a few
 // microseconds each, plus a host synchronisation for the moments).  Here every column tile of
 // every graph becomes a set of edge-block work items; one persistent cooperative kernel walks
-// all items of step s, meets the other blocks at a grid barrier, and moves on to step s + 1,
+// items in (wave, step, item) order, each waiting only for the previous step of its own tile,
 // so a whole batch costs one launch.  The launch (with the memsets it needs) is captured in a
 // CUDA graph once per plan and replayed.  Each graph's column tile comes from an autotuner
 // that times the step kernel on the largest graph of each size class for the candidate tile
@@ -267,11 +267,20 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   B_CUDA(cudaMemcpyAsync(ctx->b_items.ptr, items_h.data(), items_h.size() * 4, cudaMemcpyHostToDevice, s));
   if (wave_end.empty() || wave_end.back() != nitems) wave_end.push_back(nitems);
   const int nwaves = (int)wave_end.size();
-  B_ALLOC(csc::ensure(ctx->b_waves, wave_end.size() * 8));
-  const size_t work_bytes = (size_t)nwaves * (m + 1) * 4;
+  // claim_end[w]: cumulative (step, item) claims through wave w
+  std::vector<int64_t> waves_h(wave_end);
+  for (int w = 0, prev = 0; w < nwaves; ++w) {
+    const int64_t before = w > 0 ? waves_h[nwaves + w - 1] : 0;
+    waves_h.push_back(before + (int64_t)(m + 1) * (wave_end[w] - prev));
+    prev = (int)wave_end[w];
+  }
+  B_ALLOC(csc::ensure(ctx->b_waves, waves_h.size() * 8));
+  B_CUDA(cudaMemcpyAsync(ctx->b_waves.ptr, waves_h.data(), waves_h.size() * 8, cudaMemcpyHostToDevice, s));
+  // b_work: the claim counter, then done[tiles][m + 1]
+  const size_t work_bytes = 8 + (size_t)total_tiles * (m + 1) * 4;
   B_ALLOC(csc::ensure(ctx->b_work, work_bytes));
-  unsigned int* work = static_cast<unsigned int*>(ctx->b_work.ptr);
-  B_CUDA(cudaMemcpyAsync(ctx->b_waves.ptr, wave_end.data(), wave_end.size() * 8, cudaMemcpyHostToDevice, s));
+  unsigned long long* work = static_cast<unsigned long long*>(ctx->b_work.ptr);
+  unsigned int* done = reinterpret_cast<unsigned int*>(work + 1);
   ctx->batched_waves = nwaves;
 
   // ---- the persistent launch, captured once per plan signature and replayed
@@ -280,11 +289,13 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   const csc::BatchTile* tiles_d = static_cast<const csc::BatchTile*>(ctx->b_tiles.ptr);
   const int32_t* items_d = static_cast<const int32_t*>(ctx->b_items.ptr);
   const int64_t* waves_d = static_cast<const int64_t*>(ctx->b_waves.ptr);
+  const int64_t* claims_d = waves_d + nwaves;
   const size_t mom_bytes = (size_t)n_graphs * rows * 8;
   const std::vector<uint64_t> sig = {(uint64_t)(uintptr_t)tiles_d, (uint64_t)(uintptr_t)items_d,
                                      (uint64_t)nitems, (uint64_t)m, (uint64_t)grid,
                                      (uint64_t)(uintptr_t)waves_d, (uint64_t)nwaves, (uint64_t)(uintptr_t)work,
-                                     (uint64_t)(uintptr_t)bar, (uint64_t)(uintptr_t)mbase, mom_bytes};
+                                     (uint64_t)total_tiles, (uint64_t)(uintptr_t)bar, (uint64_t)(uintptr_t)mbase,
+                                     mom_bytes};
   bool replayed = false;
   if (ctx->b_exec == nullptr || ctx->b_sig != sig) {
     if (ctx->b_exec) {
@@ -298,8 +309,8 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
       const bool body = cudaMemsetAsync(mbase, 0, mom_bytes, ctx->b_cap) == cudaSuccess &&
                         cudaMemsetAsync(bar, 0, 32, ctx->b_cap) == cudaSuccess &&
                         cudaMemsetAsync(work, 0, work_bytes, ctx->b_cap) == cudaSuccess &&
-                        csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, work, bar, err, grid,
-                                                 ctx->b_cap) == cudaSuccess;
+                        csc::launch_cheb_batched(tiles_d, items_d, waves_d, claims_d, nwaves, m, work, done, err,
+                                                 grid, ctx->b_cap) == cudaSuccess;
       ok = cudaStreamEndCapture(ctx->b_cap, &graph) == cudaSuccess && body && graph != nullptr;
     }
     if (ok) ok = cudaGraphInstantiate(&ctx->b_exec, graph, 0) == cudaSuccess;
@@ -319,7 +330,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     B_CUDA(cudaMemsetAsync(mbase, 0, mom_bytes, s));
     B_CUDA(cudaMemsetAsync(bar, 0, 32, s));
     B_CUDA(cudaMemsetAsync(work, 0, work_bytes, s));
-    B_CUDA(csc::launch_cheb_batched(tiles_d, items_d, waves_d, nwaves, m, work, bar, err, grid, s));
+    B_CUDA(csc::launch_cheb_batched(tiles_d, items_d, waves_d, claims_d, nwaves, m, work, done, err, grid, s));
   }
   ctx->batched_launches += 1;
   ctx->graph_replays += replayed ? 1 : 0;
@@ -337,7 +348,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   B_CUDA(cudaMemcpyAsync(ef.data(), mbase, mom_bytes, cudaMemcpyDeviceToHost, s));
   B_CUDA(cudaMemcpyAsync(&err_h, err, 4, cudaMemcpyDeviceToHost, s));
   B_CUDA(cudaStreamSynchronize(s));
-  if (err_h != 0) return fail(ctx, CSC_ETIMEOUT, "csc_filter_batched: a grid barrier wait expired");
+  if (err_h != 0) return fail(ctx, CSC_ETIMEOUT, "csc_filter_batched: a bounded dependency wait expired");
   if (mu_out) {
     for (int g = 0; g < n_graphs; ++g) {
       const double* e = ef.data() + (size_t)g * rows;

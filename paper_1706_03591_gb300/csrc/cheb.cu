@@ -565,51 +565,76 @@ __device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
   }
 }
 
-// Waves keep the working set of the tiles in flight near the L2 size: every tile of a wave runs
-// all m + 1 steps before the next wave starts.
-// Items are claimed dynamically (one counter per wave and step) because their cost varies
-// with the tile width of their graph.
+// Dataflow schedule.  Work items are claimed from one counter in (wave, step, item) order;
+// waves keep the working set of the tiles in flight near the L2 size.  Step s of a tile reads
+// that tile's blocks of steps s - 1 and s - 2 and overwrites the one of step s - 3, so an item
+// of step s waits (bounded) until every item of step s - 1 of its own tile is done; no grid
+// barrier is needed, fast tiles run ahead, and the next wave starts while the last steps of
+// the current one finish.  A claimed item only waits on items with smaller claim numbers, and
+// all blocks are co-resident (cooperative launch), so the schedule cannot deadlock.
 __global__ void __launch_bounds__(kBlock, 3) cheb_batched_kernel(const BatchTile* __restrict__ tiles,
                                                                  const int32_t* __restrict__ item_tile,
                                                                  const int64_t* __restrict__ wave_end,
+                                                                 const int64_t* __restrict__ claim_end,
                                                                  int nwaves, int m,
-                                                                 unsigned int* work, unsigned int* bar,
-                                                                 int* err) {
+                                                                 unsigned long long* work,
+                                                                 unsigned int* done, int* err) {
   __shared__ BatchSmem st;
   __shared__ int64_t claim;
-  int64_t w0 = 0;
-  for (int wv = 0; wv < nwaves; ++wv) {
-    const int64_t w1 = __ldg(wave_end + wv);
-    for (int s = 0; s <= m; ++s) {
-      unsigned int* ctr = work + (size_t)wv * (m + 1) + s;
-      for (;;) {
-        __syncthreads();  // every thread has read the previous claim
-        if (threadIdx.x == 0) claim = w0 + (int64_t)atomicAdd(ctr, 1u);
-        __syncthreads();
-        const int64_t it = claim;
-        if (it >= w1) break;
-        const int ti = __ldg(item_tile + it);
-        const BatchTile& t = tiles[ti];
-        const int b = (int)(it - t.blk0);
-        if (s == 0) {
-          switch (t.lpr) {
-            case 2: batched_signals<2>(t, b); break;
-            case 4: batched_signals<4>(t, b); break;
-            case 8: batched_signals<8>(t, b); break;
-            default: batched_signals<16>(t, b); break;
+  __shared__ int ready;
+  const int64_t total = claim_end[nwaves - 1];
+  for (;;) {
+    __syncthreads();  // every thread has read the previous claim
+    if (threadIdx.x == 0) claim = (int64_t)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t q = claim;
+    if (q >= total) break;
+    int wv = 0;
+    while (claim_end[wv] <= q) ++wv;
+    const int64_t c0 = wv > 0 ? claim_end[wv - 1] : 0, w0 = wv > 0 ? wave_end[wv - 1] : 0;
+    const int64_t items = wave_end[wv] - w0;
+    const int s = (int)((q - c0) / items);
+    const int64_t it = w0 + (q - c0) % items;
+    const int ti = __ldg(item_tile + it);
+    const BatchTile& t = tiles[ti];
+    const int b = (int)(it - t.blk0);
+    if (s >= 1) {
+      if (threadIdx.x == 0) {
+        volatile unsigned int* dep = done + (size_t)ti * (m + 1) + (s - 1);
+        long long spins = 0;
+        int ok = 1;
+        while (*dep < (unsigned int)t.a.nblk) {
+          if (++spins > (1ll << 23) || *(volatile int*)err != 0) {
+            atomicExch(err, 1);
+            ok = 0;
+            break;
           }
-        } else {
-          switch (t.lpr) {
-            case 2: batched_item<2>(t, st, b, s); break;
-            case 4: batched_item<4>(t, st, b, s); break;
-            case 8: batched_item<8>(t, st, b, s); break;
-            default: batched_item<16>(t, st, b, s); break;
-          }
+          __nanosleep(64);
         }
+        __threadfence();
+        ready = ok;
       }
-      if (!grid_barrier(bar, err)) return;
+      __syncthreads();
+      if (!ready) return;
     }
-    w0 = w1;
+    if (s == 0) {
+      switch (t.lpr) {
+        case 2: batched_signals<2>(t, b); break;
+        case 4: batched_signals<4>(t, b); break;
+        case 8: batched_signals<8>(t, b); break;
+        default: batched_signals<16>(t, b); break;
+      }
+    } else {
+      switch (t.lpr) {
+        case 2: batched_item<2>(t, st, b, s); break;
+        case 4: batched_item<4>(t, st, b, s); break;
+        case 8: batched_item<8>(t, st, b, s); break;
+        default: batched_item<16>(t, st, b, s); break;
+      }
+    }
+    __threadfence();  // this item's blocks are visible before it is counted
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(done + (size_t)ti * (m + 1) + s, 1u);
   }
 }
 
@@ -708,10 +733,10 @@ int cheb_batched_grid() {
 }
 
 cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, const int64_t* wave_end,
-                                int nwaves, int m, unsigned int* work, unsigned int* barrier, int* err, int grid,
-                                cudaStream_t s) {
-  void* args[] = {(void*)&tiles, (void*)&item_tile, (void*)&wave_end, (void*)&nwaves, (void*)&m,
-                  (void*)&work, (void*)&barrier, (void*)&err};
+                                const int64_t* claim_end, int nwaves, int m, unsigned long long* work,
+                                unsigned int* done, int* err, int grid, cudaStream_t s) {
+  void* args[] = {(void*)&tiles, (void*)&item_tile, (void*)&wave_end, (void*)&claim_end, (void*)&nwaves,
+                  (void*)&m, (void*)&work, (void*)&done, (void*)&err};
   return cudaLaunchCooperativeKernel((const void*)cheb_batched_kernel, dim3(grid), dim3(kBlock), args,
                                      0, s);
 }

@@ -129,13 +129,14 @@ struct BatchTile {
 // Persistent cooperative launch over all tiles: signals, first step and m-1 steps separated
 // by grid barriers (bounded spin; a timeout sets *err = 1 and every block returns).
 // item_tile[i] = tile of flat edge-block item i (nitems items).
-// Persistent cooperative launch over the item list, wave by wave: items [wave_end[w-1],
-// wave_end[w]) run all m + 1 steps (signals, first step, m - 1 general steps), a bounded grid
-// barrier after each step, before the next wave starts.
-// work: [nwaves][m + 1] zeroed item counters (claimed dynamically by the CTAs).
+// Persistent cooperative launch over the item list: items [wave_end[w-1], wave_end[w]) run all
+// m + 1 steps (signals, first step, m - 1 general steps); claim_end[w] is the cumulative number
+// of (step, item) claims up to wave w.  work (one zeroed counter) hands out the claims; done
+// ([tiles][m + 1], zeroed) counts the finished items of every tile and step; *err is set when a
+// bounded dependency wait runs out.
 cudaError_t launch_cheb_batched(const BatchTile* tiles, const int32_t* item_tile, const int64_t* wave_end,
-                                int nwaves, int m, unsigned int* work, unsigned int* barrier, int* err, int grid,
-                                cudaStream_t s);
+                                const int64_t* claim_end, int nwaves, int m, unsigned long long* work,
+                                unsigned int* done, int* err, int grid, cudaStream_t s);
 int cheb_batched_grid();
 // Sums partials[(q * nslots + slot) * grid + b] over b (fixed order) into out[q * nslots + slot]
 // for q in 0..nq-1, accumulating across `tiles` consecutive partial blocks of stride tile_stride.
@@ -287,7 +288,7 @@ struct csc_ctx {
   csc::DevBuf b_waves;  // int64 [waves]: end of each wave in the item list
   csc::GradState gs;    // differentiation: checkpoints of the last csc_filter_forward
   csc::DevBuf sim;      // csc_laplacian_distance scratch: double [2n + 2 grid + 8]
-  csc::DevBuf b_work;   // uint32 [waves][m + 1]: item counters of the persistent kernel
+  csc::DevBuf b_work;   // uint64 claim counter, int64 [waves] claim ends, uint32 [tiles][m + 1] done counts
   cudaStream_t b_cap = nullptr;
   cudaGraphExec_t b_exec = nullptr;
   std::vector<uint64_t> b_sig;              // launch signature of b_exec

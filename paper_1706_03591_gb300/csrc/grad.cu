@@ -70,6 +70,7 @@ struct AdjArgs {
   float cj;             // 1 for j == 0, 2 otherwise
   float* H;             // [nnz]
   double* part;         // [grid]: partial sums of <G, T_j R>
+  int l2pf;             // prefetch the next batch of gathered rows into L2
 };
 
 // One reverse step: row-parallel, the LPR = w / 4 lanes of a slot own a row.
@@ -101,7 +102,19 @@ __global__ void __launch_bounds__(kBlk, 3) adjoint_step_kernel(AdjArgs a) {
     int maxlen = len;
     for (int off = 16; off > 0; off >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kAll, maxlen, off));
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    constexpr int kLines = LPR >= 8 ? LPR / 8 : 1;  // 128-byte lines per gathered row
     for (int e0 = 0; e0 < maxlen; e0 += kEdgeUnroll) {
+      if (a.l2pf) {
+        // the next batch's rows of both gathered blocks into L2 while this batch loads
+        for (int q = sub; q < 2 * kEdgeUnroll * kLines; q += LPR) {
+          const int u = q / (2 * kLines), rest = q % (2 * kLines);
+          if (e0 + kEdgeUnroll + u < len) {
+            const int c = __ldg(a.col + beg + e0 + kEdgeUnroll + u);
+            const float* src = (rest < kLines ? a.phi1 : a.vj) + (int64_t)c * w + (rest % kLines) * 32;
+            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(src) : "memory");
+          }
+        }
+      }
       float4 pv[kEdgeUnroll], vv[kEdgeUnroll];
       float wt[kEdgeUnroll], sv[kEdgeUnroll], dot[kEdgeUnroll];
 #pragma unroll
@@ -525,6 +538,7 @@ extern "C" csc_status csc_filter_vjp(csc_ctx* ctx, const float* grad_psi, int64_
         a.cj = j == 0 ? 1.0f : 2.0f;
         a.H = csc::as<float>(gs.H);
         a.part = part;
+        a.l2pf = (double)n * w * 8.0 > 64.0 * (1 << 20);  // two gathered blocks of n x w floats
         G_CUDA(csc::launch_adjoint(a, agrid, s));
         csc::sum_partials_kernel<<<1, csc::kBlk, 0, s>>>(part, agrid, ga_dev + (size_t)j * gs.ntiles + tile);
         G_CUDA(cudaGetLastError());
