@@ -251,12 +251,13 @@ typedef struct csc_graph_desc {
  * Psi~_g = h_g(L_g) R_g with R_g its counter-based signals (stored in bfloat16 when the
  * context precision is CSC_BF16, else float32), the order-m Jackson-damped low-pass of
  * cutoff lambda_c, and its trace moments (Sections 2.2 and 3.3).  All recursion steps of all
- * graphs run in one persistent cooperative kernel launch with bounded grid barriers between
- * steps, captured in a CUDA graph and replayed on later calls with the same plan.  The
+ * graphs run in one persistent cooperative kernel launch in which every step of a tile waits
+ * (bounded) for the previous step of that tile, captured in a CUDA graph and replayed on later
+ * calls with the same plan.  The
  * column tile of each graph is chosen by an autotuner that times the candidate tiles once per
  * graph size class (cached on the context).  Graphs must satisfy the CSR conditions of
  * csc_set_graph (not validated here).  mu_out: host double[n_graphs * (2m+1)] or NULL.
- * Errors: CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA, CSC_ETIMEOUT (a grid barrier wait expired). */
+ * Errors: CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA, CSC_ETIMEOUT (a dependency wait expired). */
 csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_graph_desc* descs, int m,
                               double* mu_out);
 

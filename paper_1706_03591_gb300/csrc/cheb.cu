@@ -464,36 +464,6 @@ __global__ void __launch_bounds__(kBlock, 4) cheb_step_kernel(StepArgs a) {
 
 // ------------------------------------------------------------------ batched filtering
 
-// Grid barrier for a cooperative launch (all blocks co-resident).  Sense by generation
-// counter; the wait is bounded (about a second), after which *err is set and false returned.
-__device__ bool grid_barrier(unsigned int* bar, int* err) {
-  __syncthreads();
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
-    volatile unsigned int* gen = bar + 1;
-    const unsigned int g = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (++spins > (1ll << 23) || *(volatile int*)err != 0) {
-          atomicExch(err, 1);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __threadfence();
-    ok = *(volatile int*)err == 0;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
 template <int NQ>
 __device__ __forceinline__ void block_atomic(double (&acc)[NQ], double* dst) {
   __shared__ double red[NQ][kBlock / 32];

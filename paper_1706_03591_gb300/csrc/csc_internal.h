@@ -126,9 +126,7 @@ struct BatchTile {
   float inv_sqrt_d;
 };
 
-// Persistent cooperative launch over all tiles: signals, first step and m-1 steps separated
-// by grid barriers (bounded spin; a timeout sets *err = 1 and every block returns).
-// item_tile[i] = tile of flat edge-block item i (nitems items).
+// item_tile[i] = tile of flat edge-block item i.
 // Persistent cooperative launch over the item list: items [wave_end[w-1], wave_end[w]) run all
 // m + 1 steps (signals, first step, m - 1 general steps); claim_end[w] is the cumulative number
 // of (step, item) claims up to wave w.  work (one zeroed counter) hands out the claims; done
