@@ -20,6 +20,21 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def fp32_floor(lt, r, m, lam, ref):
+    """Error of a plain float32 evaluation of the same recursion against float64 (the rounding
+    floor any float32 implementation meets; large when the filter output cancels, e.g. h(1)
+    for an edgeless graph with a cutoff below 1)."""
+    lt32 = lt.astype(np.float32)
+    a32 = cb.filter_coefficients(m, lam).astype(np.float32)
+    t_prev = r.astype(np.float32)
+    t_cur = lt32 @ t_prev
+    out = a32[0] * t_prev + a32[1] * t_cur
+    for j in range(2, m + 1):
+        t_prev, t_cur = t_cur, 2.0 * (lt32 @ t_cur) - t_prev
+        out += a32[j] * t_cur
+    return rel(out, ref)
+
+
 def _batch(seed=0, count=7):
     """Uneven graphs: SBM and Chung-Lu, n from 150 to 6000, k from 5 to 20, d = 4k (ragged tiles)."""
     rng = np.random.default_rng(seed)
@@ -96,3 +111,43 @@ def test_batched_replay_and_per_graph_agreement(gpu_lib):
             mu_ref = ctx.cheb_filter(m, b["lam"], r, ref)
             assert rel(d["psi"].cpu().numpy(), ref.cpu().numpy()) < FP32_TOL
             assert np.max(np.abs(mu_g - mu_ref)) < FP32_TOL * mu_ref[0]
+
+
+def test_batched_weighted_edgeless_tiny_and_several_waves(gpu_lib):
+    """A weighted graph, an edgeless graph, a single node, and a 3e5-node graph with 256 columns
+    whose four 64-column tiles each exceed the wave budget (so the schedule crosses waves);
+    every graph against the oracle (sampled columns for the large one)."""
+    m = 30
+    rng = np.random.default_rng(9)
+    gw = W.sbm_graph(500, 5, 12, 10, seed=41)
+    rows = np.repeat(np.arange(gw.n), np.diff(gw.row_ptr))
+    key = np.minimum(rows, gw.col_idx).astype(np.int64) * gw.n + np.maximum(rows, gw.col_idx)
+    _, inv = np.unique(key, return_inverse=True)
+    wvals = rng.uniform(0.5, 2.0, inv.max() + 1)[inv].astype(np.float32)
+    class Csr:  # edgeless graphs as plain CSR
+        def __init__(self, n):
+            self.n, self.row_ptr, self.col_idx = n, np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32)
+
+    big = W.sbm_graph(300_000, 10, 10, 10, seed=42)
+    cases = [(gw, wvals, 20, 0.7), (Csr(50), None, 12, 0.5), (Csr(1), None, 4, 0.9), (big, None, 256, 0.4)]
+    descs = []
+    for i, (g, vals, c, lam) in enumerate(cases):
+        descs.append(dict(n=g.n, row_ptr=torch.from_numpy(g.row_ptr).cuda(),
+                          col_idx=torch.from_numpy(g.col_idx).cuda(),
+                          vals=None if vals is None else torch.from_numpy(vals).cuda(),
+                          c=c, d=c, lambda_c=lam, seed=77 + i, psi=torch.zeros((g.n, c), device="cuda")))
+    with gpu_lib.Context() as ctx:
+        mu = ctx.filter_batched(descs, m)
+        st = ctx.stats()
+    assert st["batched_waves"] >= 4
+    for i, ((g, vals, c, lam), dsc) in enumerate(zip(cases, descs)):
+        lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx, vals)
+        cols = np.arange(c) if g.n < 1000 else np.array([0, 70, 150, 255])
+        r = gaussian_columns(77 + i, g.n, cols, c)
+        ref = cb.cheb_filter(lt, r, m, lam)
+        got = dsc["psi"].cpu().numpy()[:, cols]
+        tol = max(FP32_TOL, 2.0 * fp32_floor(lt, r, m, lam, ref))
+        assert rel(got, ref) < tol, (i, rel(got, ref), tol)
+        if g.n < 1000:
+            mu_ref = cb.moments(lt, r, 2 * m)
+            assert np.max(np.abs(mu[i] - mu_ref)) < FP32_TOL * mu_ref[0], i

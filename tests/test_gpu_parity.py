@@ -111,6 +111,42 @@ def test_cheb_filter_weighted_and_isolated(gpu_lib):
     assert rel(psi.cpu().numpy(), cb.cheb_filter(lt, r.astype(np.float64), 40, 0.8)) < FP32_TOL
 
 
+def _hub_graph(n=20000, deg=10, hubs=3, hub_degree=7000, seed=8):
+    """Sparse random graph plus a few hubs of very high degree (CSR, symmetric, no self-loops):
+    every row block holding a hub has more edges than the step kernel stages in shared memory."""
+    rng = np.random.default_rng(seed)
+    m = n * deg // 2
+    u = rng.integers(0, n, m)
+    v = rng.integers(0, n, m)
+    hub_ids = rng.choice(n, hubs, replace=False)
+    hu = np.repeat(hub_ids, hub_degree)
+    hv = rng.integers(0, n, hubs * hub_degree)
+    u, v = np.concatenate([u, hu]), np.concatenate([v, hv])
+    keep = u != v
+    u, v = u[keep], v[keep]
+    keys = np.unique(np.concatenate([u * n + v, v * n + u]))
+    rows, cols = keys // n, keys % n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return n, np.cumsum(row_ptr), cols.astype(np.int32)
+
+
+@pytest.mark.parametrize("tile", [8, 32, 64])
+def test_cheb_filter_hub_rows_beyond_the_staging_buffer(gpu_lib, tile):
+    n, rp, ci = _hub_graph()
+    assert np.diff(rp).max() > 5632  # one hub row alone exceeds the staged edge buffer
+    lt = lp.shifted_laplacian(n, rp, ci)
+    r = W.gaussian_block(n, 40, 64, seed=9)
+    with gpu_lib.Context({"col_tile": tile}) as ctx:
+        ctx.set_graph(n, dev(rp), dev(ci))
+        psi = torch.zeros((n, 40), device="cuda")
+        mu = ctx.cheb_filter(50, 0.7, dev(r), psi)
+    ref = cb.cheb_filter(lt, r.astype(np.float64), 50, 0.7)
+    assert rel(psi.cpu().numpy(), ref) < FP32_TOL
+    mu_ref = cb.moments(lt, r.astype(np.float64), 100)
+    assert np.max(np.abs(mu - mu_ref)) < FP32_TOL * mu_ref[0]
+
+
 def test_cheb_filter_edgeless_graph(gpu_lib):
     n = 257
     g_rp = np.zeros(n + 1, dtype=np.int64)
