@@ -5,6 +5,8 @@
 // columns); in the same pass every row is normalised, y_i = theta_i / ||theta_i||
 // (a zero row stays zero), for the k-means step.  One warp per row; the row's d values
 // stay in registers between the norm and the scaled write.
+#include <type_traits>
+
 #include "csc_internal.h"
 
 namespace csc {
@@ -24,7 +26,8 @@ __device__ __forceinline__ void put<__nv_bfloat16>(__nv_bfloat16* p, float v) {
 __device__ __forceinline__ float get(const float* p) { return *p; }
 __device__ __forceinline__ float get(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
-template <typename TY>
+// PER: values per lane (d <= 32 PER), so a row lives in registers without dead slots.
+template <typename TY, int PER>
 __global__ void assemble_kernel(float* __restrict__ theta, int64_t ldt, const float* __restrict__ psi,
                                 int64_t ldp, const int* __restrict__ src, int d, TY* __restrict__ y,
                                 int64_t ldy, int64_t n) {
@@ -32,10 +35,10 @@ __global__ void assemble_kernel(float* __restrict__ theta, int64_t ldt, const fl
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = warp; row < n; row += nwarps) {
-    float v[kMaxPerLane];
+    float v[PER];
     float ss = 0.f;
 #pragma unroll
-    for (int i = 0; i < kMaxPerLane; ++i) {
+    for (int i = 0; i < PER; ++i) {
       const int q = lane + 32 * i;
       v[i] = 0.f;
       if (q < d) {
@@ -53,7 +56,7 @@ __global__ void assemble_kernel(float* __restrict__ theta, int64_t ldt, const fl
     for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
     const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
 #pragma unroll
-    for (int i = 0; i < kMaxPerLane; ++i) {
+    for (int i = 0; i < PER; ++i) {
       const int q = lane + 32 * i;
       if (q < d) put<TY>(y + row * ldy + q, v[i] * inv);
     }
@@ -88,11 +91,20 @@ cudaError_t launch_assemble(float* theta, int64_t ldt, const float* psi, int64_t
   if (n == 0) return cudaSuccess;
   if (d > 32 * kMaxPerLane) return cudaErrorInvalidValue;
   const int grid = grid_rows(n, 8);
-  if (y_dtype == CSC_BF16)
-    assemble_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(theta, ldt, psi, ldp, src, d,
-                                                        (__nv_bfloat16*)y, ldy, n);
-  else
-    assemble_kernel<float><<<grid, 256, 0, s>>>(theta, ldt, psi, ldp, src, d, (float*)y, ldy, n);
+  auto go = [&](auto per) {
+    constexpr int P = decltype(per)::value;
+    if (y_dtype == CSC_BF16)
+      assemble_kernel<__nv_bfloat16, P><<<grid, 256, 0, s>>>(theta, ldt, psi, ldp, src, d, (__nv_bfloat16*)y,
+                                                             ldy, n);
+    else
+      assemble_kernel<float, P><<<grid, 256, 0, s>>>(theta, ldt, psi, ldp, src, d, (float*)y, ldy, n);
+  };
+  if (d <= 32) go(std::integral_constant<int, 1>{});
+  else if (d <= 64) go(std::integral_constant<int, 2>{});
+  else if (d <= 128) go(std::integral_constant<int, 4>{});
+  else if (d <= 256) go(std::integral_constant<int, 8>{});
+  else if (d <= 512) go(std::integral_constant<int, 16>{});
+  else go(std::integral_constant<int, 32>{});
   return cudaGetLastError();
 }
 
