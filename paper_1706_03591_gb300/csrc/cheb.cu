@@ -162,8 +162,10 @@ struct StageRows {
   int rp[kStepRows + 1];
 };
 
-// Stages rows [rs, re): row offsets, columns (and weights when the graph is weighted).
+// Stages rows [rs, re): row offsets, columns, and the per-edge weights when the graph is
+// weighted or SCALED (first step: w_uv D^-1/2_v, since T_0 = R is unscaled).
 // Returns false when the edges exceed the buffer (the block then reads global memory).
+template <bool SCALED = false>
 __device__ __forceinline__ bool stage_rows(const StepArgs& a, StageRows& st, int rs, int re) {
   const int64_t es = __ldg(a.row_ptr + rs);
   const int64_t ee = __ldg(a.row_ptr + re);
@@ -180,13 +182,14 @@ __device__ __forceinline__ bool stage_rows(const StepArgs& a, StageRows& st, int
       const int e = base + u * blockDim.x + threadIdx.x;
       c[u] = e < ne ? __ldcs(a.col + es + e) : 0;
       v[u] = (e < ne && weighted) ? __ldcs(a.val + es + e) : 1.0f;
+      if (SCALED && e < ne) v[u] *= __ldg(a.scale + c[u]);
     }
 #pragma unroll
     for (int u = 0; u < kStageUnroll; ++u) {
       const int e = base + u * blockDim.x + threadIdx.x;
       if (e < ne) {
         st.col[e] = c[u];
-        if (weighted) st.wt[e] = v[u];
+        if (SCALED || weighted) st.wt[e] = v[u];
       }
     }
   }
@@ -305,33 +308,26 @@ __device__ __forceinline__ void first_block(const StepArgs& a, Stage& st, int b,
   }
 }
 
-template <int LPR, typename T0>
-__global__ void __launch_bounds__(kBlock) cheb_first_kernel(StepArgs a) {
-  __shared__ Stage st;
-  double acc[3] = {0.0, 0.0, 0.0};  // <T0,T0>, <T1,T1>, <T1,T0>
-  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) first_block<LPR, T0>(a, st, b, acc);
-  block_store<3>(acc, a.part);
-}
 
 // Row-parallel variant of the gather for the general step: the LPR lanes of one slot own
 // one row; kRowUnroll predicated 16-byte loads per lane are in flight per batch.
 constexpr int kRowUnroll = 8;
 
-template <int LPR, typename ST>
+template <int LPR, typename ST, bool SCALED = false, typename TG = float>
 __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const ST& st, bool staged,
-                                                 const float* __restrict__ tg, int64_t row, int rl,
+                                                 const TG* __restrict__ tg, int64_t row, int rl,
                                                  bool valid, int sub) {
   const int w = a.w;
-  const float* base = tg + sub * 4;
+  const TG* base = tg + sub * 4;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!valid) return acc;
   if (staged) {
     const int beg = st.rp[rl], end = st.rp[rl + 1];
-    const bool weighted = a.val != nullptr;
+    const bool weighted = SCALED || a.val != nullptr;
     const uint64_t keep = l2_keep();
     constexpr int kLines = LPR >= 8 ? LPR / 8 : 1;  // 128-byte lines per gathered row
     for (int e0 = beg; e0 < end; e0 += kRowUnroll) {
-      if (a.l2pf) {
+      if (!SCALED && a.l2pf) {
         // the next batch's rows into L2 while this batch loads: more misses in flight without
         // holding registers (pays off when the gathered block exceeds the L2)
         for (int q = sub; q < kRowUnroll * kLines; q += LPR) {
@@ -362,11 +358,88 @@ __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const ST& st
     const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
     for (int64_t e = beg; e < end; ++e) {
       const int c = __ldg(a.col + e);
-      const float wv = a.val != nullptr ? __ldg(a.val + e) : 1.0f;
+      float wv = a.val != nullptr ? __ldg(a.val + e) : 1.0f;
+      if (SCALED) wv *= __ldg(a.scale + c);
       fma4(acc, wv, ld4(base + (int64_t)c * w));
     }
   }
   return acc;
+}
+
+// One row block of the first step (row-parallel, as the general step): T_1 = L~ T_0 =
+// -D^-1/2 W D^-1/2 R, stored as V_1 = vs T_1; Psi = a_0 T_0 + a_1 T_1; partials <T_0,T_0>,
+// <T_1,T_1>, <T_1,T_0> accumulated into acc (first lane of each slot).
+template <int LPR, typename T0>
+__device__ __forceinline__ void first_rows(const StepArgs& a, StageRows& st, int b, double (&acc)[3]) {
+  constexpr int S = 32 / LPR;
+  constexpr int kRowsPerPass = (kBlock / 32) * S;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int slot = lane / LPR, sub = lane % LPR;
+  const T0* __restrict__ t0 = static_cast<const T0*>(a.tg);
+  const int w = a.w;
+  float a0 = 0.f, a1 = 0.f;
+  if (a.psi != nullptr) { a0 = __ldg(a.coef); a1 = __ldg(a.coef + 1); }
+  const int rs = b * a.rpb;
+  const int re = (int)min((int64_t)rs + a.rpb, a.n);
+  __syncthreads();
+  const bool staged = stage_rows<true>(a, st, rs, re);
+  __syncthreads();
+  for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
+    const int r = r0 + wid * S + slot;
+    const bool valid = r < re;
+    const int64_t row = valid ? r : rs;
+    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+    float si = 0.f, vsi = 0.f;
+    if (valid) {
+      own = ld4(t0 + row * w + sub * 4);
+      si = -__ldg(a.scale + row);
+      vsi = __ldg(a.vs + row);
+    }
+    const float4 g = gather_own_row<LPR, StageRows, true, T0>(a, st, staged, t0, row, r - rs, valid, sub);
+    float e0 = 0.f, e1 = 0.f, f1 = 0.f;
+    if (valid) {
+      const float4 t1 = make_float4(si * g.x, si * g.y, si * g.z, si * g.w);
+      st4(a.tn + row * w + sub * 4, make_float4(vsi * t1.x, vsi * t1.y, vsi * t1.z, vsi * t1.w));
+      if (a.psi != nullptr) {
+        float4 p;
+        p.x = fmaf(a1, t1.x, a0 * own.x);
+        p.y = fmaf(a1, t1.y, a0 * own.y);
+        p.z = fmaf(a1, t1.z, a0 * own.z);
+        p.w = fmaf(a1, t1.w, a0 * own.w);
+        st4(a.psi + row * a.ldp + sub * 4, p);
+      }
+      e0 = dot4(own, own);
+      e1 = dot4(t1, t1);
+      f1 = dot4(t1, own);
+    }
+#pragma unroll
+    for (int off = 1; off < LPR; off <<= 1) {
+      e0 += __shfl_xor_sync(kFull, e0, off);
+      e1 += __shfl_xor_sync(kFull, e1, off);
+      f1 += __shfl_xor_sync(kFull, f1, off);
+    }
+    if (sub == 0 && valid) {
+      acc[0] += (double)e0;
+      acc[1] += (double)e1;
+      acc[2] += (double)f1;
+    }
+  }
+}
+
+template <int LPR, typename T0>
+__global__ void __launch_bounds__(kBlock, 4) cheb_first_kernel(StepArgs a) {
+  __shared__ StageRows st;
+  double acc[3] = {0.0, 0.0, 0.0};  // <T0,T0>, <T1,T1>, <T1,T0>
+  const int nb = (int)((a.n + a.rpb - 1) / a.rpb);
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) first_rows<LPR, T0>(a, st, b, acc);
+  // every lane may hold a partial: reduce the warp first
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc[0] += __shfl_xor_sync(kFull, acc[0], off);
+    acc[1] += __shfl_xor_sync(kFull, acc[1], off);
+    acc[2] += __shfl_xor_sync(kFull, acc[2], off);
+  }
+  block_store<3>(acc, a.part);
 }
 
 // One block of a general step (row-parallel: the LPR lanes of a slot own a row):
@@ -672,11 +745,21 @@ int cheb_grid(int w) {
   return grid;
 }
 
+// Rows per block of the row-parallel kernels: whole passes of the row slots, at most kStepRows,
+// about two blocks per CTA of the grid on small graphs.
+int rows_per_block(int64_t n, int lpr, int grid) {
+  const int64_t rpp = (kBlock / 32) * (32 / lpr);
+  const int64_t want = (n + 2 * (int64_t)grid - 1) / (2 * (int64_t)grid);
+  return (int)std::min<int64_t>(kStepRows, std::max<int64_t>(rpp, (want + rpp - 1) / rpp * rpp));
+}
+
 cudaError_t launch_cheb_first(const StepArgs& a, int t0_dtype, int grid, cudaStream_t s) {
   const int lpr = a.w / 4;
   const void* fn = t0_dtype == CSC_BF16 ? first_kernel_for<__nv_bfloat16>(lpr)
                                         : first_kernel_for<float>(lpr);
-  return launch_any(fn, a, grid, s);
+  StepArgs b = a;
+  b.rpb = rows_per_block(a.n, lpr, grid);
+  return launch_any(fn, b, grid, s);
 }
 
 cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStream_t s) {
@@ -684,9 +767,7 @@ cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStre
   const void* fn = tp_dtype == CSC_BF16 ? step_kernel_for<__nv_bfloat16>(lpr)
                                         : step_kernel_for<float>(lpr);
   StepArgs b = a;
-  const int64_t rpp = (kBlock / 32) * (32 / lpr);  // rows per pass of the row slots
-  const int64_t want = (a.n + 2 * (int64_t)grid - 1) / (2 * (int64_t)grid);
-  b.rpb = (int)std::min<int64_t>(kStepRows, std::max<int64_t>(rpp, (want + rpp - 1) / rpp * rpp));
+  b.rpb = rows_per_block(a.n, lpr, grid);
   b.l2pf = (double)a.n * a.w * 4.0 > 64.0 * (1 << 20);
   return launch_any(fn, b, grid, s);
 }
