@@ -1,9 +1,9 @@
 """k-means on the feature rows (Section 2.1, Eq. 1 and Eq. 2).  Test infrastructure only.
 
-The paper asks for "a k-means assignment" of the feature rows and measures it
-with C_X = ||Phi - X X^T Phi||_F, X the n x k indicator with X_ij = 1/sqrt(s_j)
-(Eq. 1-2); C_X^2 is the usual within-cluster sum of squares.  It does not fix
-the algorithm; the readings taken here are Lloyd's iteration with
+The paper clusters the feature rows with k-means and measures the result with
+C_X = ||Phi - X X^T Phi||_F, X the n x k indicator with X_ij = 1/sqrt(s_j) (Eq. 1-2);
+C_X^2 is the usual within-cluster sum of squares.  It does not fix the algorithm; the
+readings taken here are Lloyd's iteration with
 
 * initial centroids given by the caller: Forgy (k row indices) or a warm start
   (means of the previous snapshot's assignment on the new features, an empty
