@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 2
+#define CSC_ABI_VERSION 3
 
 typedef struct csc_ctx csc_ctx;
 
@@ -330,6 +330,48 @@ csc_status csc_kmeans_loss_grad(csc_ctx* ctx, const float* psi, int64_t ldp, int
 csc_status csc_laplacian_distance(csc_ctx* ctx, int64_t n, const int64_t* rp_a, const int32_t* col_a,
                                   const float* val_a, const int64_t* rp_b, const int32_t* col_b,
                                   const float* val_b, double* rho_out);
+
+/* ---------------------------------------------------------------- compressive k-means */
+
+/* Compressive k-means (Section 2.2, step 2; cost counted in Section 4.2): k-means on a
+ * variable-density sample of the nodes, the other assignments inferred by a Tikhonov
+ * interpolation made of k graph filterings.
+ *
+ * 1. Sampling.  Node i is drawn with probability proportional to s_i = ||theta_i||^2 (the
+ *    energy of its row of the unnormalised filtered signals), made exact in integers:
+ *    s_i = float64 sum over columns in order of theta_il^2, q_i = floor(s_i 2^E) with
+ *    E = 62 - ceil(log2 n) - e, 2^(e-1) <= max s < 2^e; P = inclusive prefix sums of q, T = P[n-1].
+ *    Draw t (t < n_draws) uses Philox-4x32-10 with counter (t, 0, 0, 2) and key seed:
+ *    u = floor((x0 2^32 + x1) T / 2^64); the node is the smallest i with P[i] > u.  The
+ *    sample Omega is the set of distinct drawn nodes in increasing order.
+ * 2. Reduced k-means.  Lloyd (as csc_kmeans) on the normalised rows y_i, i in Omega, from the
+ *    Forgy rows of n_init restarts (restart r draws with key seed + r * 0x9E3779B97F4A7C15);
+ *    the lowest inertia wins, inertias within a relative 1e-6 of it counting as equal and
+ *    the lowest restart then winning.
+ * 3. Interpolation.  Z (n x k) holds w_i = T / (n q_i) at (i, a_i) for every sampled node i
+ *    with reduced label a_i; X = h(L) Z with the order-m Jackson-damped low pass of cutoff
+ *    lambda_c, the minimiser of ||x - z_j||^2 + x^T (h(L)^-1 - I) x for every column.
+ * 4. Node i is assigned the lowest j maximising X_ij.
+ *
+ * Features: theta == NULL and y == NULL take the context's current features (after
+ * csc_filter: Theta_t, its row-normalised copy, the current cutoff when lambda_c < 0 and the
+ * last filter order when m <= 0; d, ld, y_dtype and feat_where are then ignored).  Otherwise
+ * theta is float32 n x d and y (y_dtype) n x d, both with leading dimension ld, in
+ * feat_where memory, n being the loaded graph's size.
+ * n_draws <= 0 takes max(k, ceil(2 k ln k)); n_init <= 0 takes 10; max_iter <= 0 the
+ * context's.  Outputs in out_where memory: assign_out int32[n]; optional sample_out and
+ * sample_labels_out int32[min(n, n_draws)] (Omega and its reduced labels; |Omega| entries
+ * written) and interp_out float32 n x k (leading dimension ldx >= k); optional host
+ * n_sampled_out (|Omega|) and restart_out (the restart kept).  The context's moments are
+ * left as the last csc_filter set them.
+ * Errors: CSC_ESTATE (no graph; context features before csc_filter), CSC_EINVAL (bad
+ * arguments, all-zero features, fewer distinct sampled nodes than k, n_draws >= 2^31),
+ * CSC_ENOMEM, CSC_ECUDA, CSC_ETIMEOUT (a bounded wait in the k-means pass expired). */
+csc_status csc_compressive_cluster(csc_ctx* ctx, const float* theta, const void* y, int y_dtype, int d,
+                                   int64_t ld, int feat_where, int k, int64_t n_draws, int n_init,
+                                   double lambda_c, int m, uint64_t seed, int max_iter, int32_t* assign_out,
+                                   int out_where, int32_t* sample_out, int32_t* sample_labels_out,
+                                   float* interp_out, int64_t ldx, int64_t* n_sampled_out, int* restart_out);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ __all__ = [
     "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
     "csc_filter_forward", "csc_filter_vjp", "csc_kmeans_loss_grad", "cheb_filter_layer",
-    "csc_laplacian_distance",
+    "csc_laplacian_distance", "csc_compressive_cluster",
 ]
 
 
@@ -314,6 +314,46 @@ def csc_laplacian_distance(h, n: int, graph_a, graph_b) -> float:
     return rho.value
 
 
+def csc_compressive_cluster(h, k: int, theta=None, Y=None, n_draws: int = 0, n_init: int = 0,
+                            lambda_c: float = -1.0, m: int = 0, seed: int = 0, max_iter: int = 0,
+                            assign_out=None, want_sample: bool = False, interp_out=None):
+    """Compressive k-means (see include/csc.h).  theta (float32) and Y (float32 or bfloat16),
+    both n x d, or None for the context's current features.  Returns dict(assign, n_sampled,
+    restart, sample, sample_labels); assign_out and interp_out (n x k float32) may be given
+    as arrays or CUDA tensors, the sample arrays are host numpy arrays."""
+    if (theta is None) != (Y is None):
+        raise ValueError("give both theta and Y, or neither")
+    tp, tw, _, ldt = _arr(theta, "theta")
+    yp, yw, ycode, ldy = _arr(Y, "Y")
+    d = 0
+    if theta is not None:
+        if tw != yw or ldt != ldy:
+            raise ValueError("theta and Y must share memory kind and leading dimension")
+        d = int(theta.shape[1])
+    if assign_out is None:
+        raise ValueError("assign_out (int32[n]) is required")
+    ap, aw, _, _ = _arr(assign_out, "assign_out")
+    xp, xw, _, ldx = _arr(interp_out, "interp_out")
+    if interp_out is not None and xw != aw:
+        raise ValueError("interp_out must live where assign_out lives")
+    cap = int(n_draws) if n_draws > 0 else max(k, int(np.ceil(2.0 * k * np.log(max(k, 1)))))
+    sample = np.zeros(cap, dtype=np.int32) if want_sample else None
+    slabels = np.zeros(cap, dtype=np.int32) if want_sample else None
+    if want_sample and aw != _abi.CSC_HOST:
+        raise ValueError("want_sample needs host outputs (assign_out in host memory)")
+    ns, rs = C.c_int64(), C.c_int()
+    _check(_lib().csc_compressive_cluster(
+        h, tp, yp, ycode, d, ldy or d, yw, k, n_draws, n_init, lambda_c, m, seed, max_iter, ap, aw,
+        C.c_void_p(sample.ctypes.data) if sample is not None else None,
+        C.c_void_p(slabels.ctypes.data) if slabels is not None else None,
+        xp, ldx or k, C.byref(ns), C.byref(rs)), h, "csc_compressive_cluster")
+    out = dict(assign=assign_out, n_sampled=ns.value, restart=rs.value, sample=None, sample_labels=None)
+    if want_sample:
+        out["sample"] = sample[: ns.value]
+        out["sample_labels"] = slabels[: ns.value]
+    return out
+
+
 _FILTER_FN = None
 
 
@@ -418,6 +458,9 @@ class Context:
 
     def get_features(self, dst, normalized=False):
         csc_get_features(self.h, dst, normalized)
+
+    def compressive_cluster(self, k, theta=None, Y=None, **kw):
+        return csc_compressive_cluster(self.h, k, theta, Y, **kw)
 
     def get_moments(self, length):
         return csc_get_moments(self.h, length)

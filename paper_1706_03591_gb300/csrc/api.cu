@@ -154,6 +154,9 @@ std::vector<int64_t> forgy_draw(uint64_t seed, int64_t n, int k) {
   return out;
 }
 
+// Key of the Forgy draw of restart r of the reduced k-means.
+uint64_t restart_seed(uint64_t seed, int r) { return seed + (uint64_t)r * 0x9E3779B97F4A7C15ull; }
+
 // ------------------------------------------------------------------ context helpers
 
 csc_status fail(csc_ctx* ctx, csc_status s, const std::string& msg) {
@@ -417,6 +420,7 @@ void csc_destroy(csc_ctx* ctx) {
                     &ctx->gs.nsum, &ctx->gs.part, &ctx->gs.flag, &ctx->gs.ga, &ctx->gs.rcopy, &ctx->sim};
   for (DevBuf* b : bufs) csc::release(*b);
   csc::kmeans_release(ctx->km);
+  csc::compressive_release(ctx->cmp);
   delete ctx;
 }
 
@@ -821,6 +825,129 @@ csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_i
   ctx->prev_k = k;
   if (cost_out) *cost_out = std::sqrt(std::max(0.0, res.inertia));
   if (iters_out) *iters_out = res.iters;
+  return CSC_OK;
+}
+
+
+csc_status csc_compressive_cluster(csc_ctx* ctx, const float* theta, const void* y, int y_dtype, int d,
+                                   int64_t ld, int feat_where, int k, int64_t n_draws, int n_init,
+                                   double lambda_c, int m, uint64_t seed, int max_iter, int32_t* assign_out,
+                                   int out_where, int32_t* sample_out, int32_t* sample_labels_out,
+                                   float* interp_out, int64_t ldx, int64_t* n_sampled_out, int* restart_out) {
+  if (!ctx) return CSC_EINVAL;
+  if (!ctx->g.loaded) return fail(ctx, CSC_ESTATE, "csc_compressive_cluster: no graph loaded");
+  const int64_t n = ctx->g.n;
+  if (k < 1 || !assign_out || !valid_where(out_where) || (theta == nullptr) != (y == nullptr) ||
+      n_draws >= ((int64_t)1 << 31) || (interp_out && ldx < k))
+    return fail(ctx, CSC_EINVAL, "csc_compressive_cluster: bad arguments");
+  cudaStream_t s = ctx->stream;
+  csc::CompressiveState& cs = ctx->cmp;
+  const float* th = theta;
+  const void* yy = y;
+  if (theta == nullptr) {
+    if (ctx->t == 0 || ctx->ring_n != n)
+      return fail(ctx, CSC_ESTATE, "csc_compressive_cluster: call csc_filter first");
+    th = csc::as<float>(ctx->theta);
+    yy = ctx->y.ptr;
+    y_dtype = ctx->opts.precision;
+    d = ctx->ring_d;
+    ld = d;
+    if (lambda_c < 0.0) {
+      if (!ctx->has_lambda) return fail(ctx, CSC_ESTATE, "csc_compressive_cluster: no cutoff yet");
+      lambda_c = ctx->lambda;
+    }
+    if (m <= 0) m = ctx->last_m;
+  } else {
+    if (d < 1 || d > 1024 || ld < d || !valid_dtype(y_dtype) || !valid_where(feat_where))
+      return fail(ctx, CSC_EINVAL, "csc_compressive_cluster: bad feature arguments");
+    if (feat_where == CSC_HOST) {
+      const size_t esz = dtype_size(y_dtype);
+      ALLOC_OK(csc::ensure(cs.theta_stage, (size_t)n * d * 4));
+      ALLOC_OK(csc::ensure(cs.y_stage, (size_t)n * d * esz));
+      CUDA_OK(cudaMemcpy2DAsync(cs.theta_stage.ptr, (size_t)d * 4, theta, (size_t)ld * 4, (size_t)d * 4, n,
+                                cudaMemcpyHostToDevice, s));
+      CUDA_OK(cudaMemcpy2DAsync(cs.y_stage.ptr, d * esz, y, ld * esz, d * esz, n, cudaMemcpyHostToDevice, s));
+      th = csc::as<float>(cs.theta_stage);
+      yy = cs.y_stage.ptr;
+      ld = d;
+    }
+  }
+  if (m < 1 || !(lambda_c >= 0.0 && lambda_c <= 2.0))
+    return fail(ctx, CSC_EINVAL, "csc_compressive_cluster: the interpolation needs m >= 1 and a cutoff in [0, 2]");
+  if (n_draws <= 0) n_draws = std::max<int64_t>(k, (int64_t)std::ceil(2.0 * k * std::log((double)k)));
+  if (n_init <= 0) n_init = 10;
+  if (max_iter <= 0) max_iter = ctx->opts.max_iter;
+
+  // 1. variable-density draws and the sorted sample
+  CUDA_OK(csc::compressive_sample(cs, th, ld, n, d, n_draws, seed, s));
+  ctx->launches += 9;
+  long long total = 0;
+  int n_omega = 0;
+  CUDA_OK(cudaMemcpyAsync(&total, csc::as<long long>(cs.prefix) + (n - 1), 8, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaMemcpyAsync(&n_omega, csc::as<int>(cs.pos) + (n - 1), 4, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (total <= 0) return fail(ctx, CSC_EINVAL, "csc_compressive_cluster: the features are all zero");
+  if (n_omega < k)
+    return fail(ctx, CSC_EINVAL, "csc_compressive_cluster: " + std::to_string(n_omega) +
+                                     " distinct sampled nodes for k = " + std::to_string(k) + "; raise n_draws");
+  const int32_t* omega = csc::as<int32_t>(cs.omega);
+
+  // 2. reduced k-means: n_init Forgy restarts on the sampled rows, lowest inertia kept
+  ALLOC_OK(csc::ensure(cs.yo, (size_t)n_omega * d * dtype_size(y_dtype)));
+  ALLOC_OK(csc::ensure(cs.labels, (size_t)n_init * n_omega * 4));
+  CUDA_OK(csc::compressive_gather(yy, y_dtype, ld, omega, n_omega, d, cs.yo.ptr, s));
+  ctx->launches += 1;
+  std::vector<double> inertia(n_init);
+  for (int r = 0; r < n_init; ++r) {
+    const std::vector<int64_t> idx = forgy_draw(restart_seed(seed, r), n_omega, k);
+    csc::KmeansResult res;
+    csc_status st = csc::kmeans_run(ctx->km, cs.yo.ptr, y_dtype, n_omega, d, d, k, idx.data(), nullptr,
+                                    max_iter, s, &res, &ctx->err);
+    ctx->launches += res.launches;
+    ctx->kmeans_passes += res.iters;
+    ctx->kmeans_near_ties += res.near_ties;
+    if (st != CSC_OK) return st;
+    inertia[r] = res.inertia;
+    CUDA_OK(cudaMemcpyAsync(csc::as<int32_t>(cs.labels) + (size_t)r * n_omega, res.assign, (size_t)n_omega * 4,
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  const double best = *std::min_element(inertia.begin(), inertia.end());
+  int pick = 0;
+  while (!(inertia[pick] <= best * (1.0 + 1e-6))) ++pick;
+  const int32_t* labels = csc::as<int32_t>(cs.labels) + (size_t)pick * n_omega;
+
+  // 3. interpolation: X = h(L) Z, one filtering of each cluster's weighted indicator
+  const int w = tile_width(ctx, n, k);
+  const int cpad = ((k + w - 1) / w) * w;
+  ALLOC_OK(csc::ensure(cs.z, (size_t)n * k * 4));
+  ALLOC_OK(csc::ensure(cs.x, (size_t)n * cpad * 4));
+  ALLOC_OK(csc::ensure(cs.assign, (size_t)n * 4));
+  CUDA_OK(cudaMemsetAsync(cs.z.ptr, 0, (size_t)n * k * 4, s));
+  CUDA_OK(csc::compressive_rhs(cs, labels, n_omega, n, csc::as<float>(cs.z), k, s));
+  ctx->launches += 1;
+  Source src;
+  src.philox = false;
+  src.dtype = CSC_F32;
+  src.R = cs.z.ptr;
+  src.ldr = k;
+  const std::vector<double> mu_keep = ctx->mu;
+  const int m_keep = ctx->last_m;
+  csc_status st = run_filter(ctx, m, lambda_c, k, src, csc::as<float>(cs.x), cpad);
+  ctx->mu = mu_keep;
+  ctx->last_m = m_keep;
+  if (st != CSC_OK) return st;
+  CUDA_OK(csc::compressive_argmax(csc::as<float>(cs.x), cpad, n, k, csc::as<int32_t>(cs.assign), s));
+  ctx->launches += 1;
+
+  const cudaMemcpyKind kind = out_where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CUDA_OK(cudaMemcpyAsync(assign_out, cs.assign.ptr, (size_t)n * 4, kind, s));
+  if (sample_out) CUDA_OK(cudaMemcpyAsync(sample_out, omega, (size_t)n_omega * 4, kind, s));
+  if (sample_labels_out) CUDA_OK(cudaMemcpyAsync(sample_labels_out, labels, (size_t)n_omega * 4, kind, s));
+  if (interp_out)
+    CUDA_OK(cudaMemcpy2DAsync(interp_out, (size_t)ldx * 4, cs.x.ptr, (size_t)cpad * 4, (size_t)k * 4, n, kind, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (n_sampled_out) *n_sampled_out = n_omega;
+  if (restart_out) *restart_out = pick;
   return CSC_OK;
 }
 

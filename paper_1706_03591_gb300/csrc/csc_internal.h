@@ -177,6 +177,36 @@ struct GradState {
   int64_t graph_version = -1; // graph the transpose map was built for
 };
 
+// ------------------------------------------------------------------ compressive k-means (compressive.cu)
+
+// Scratch of csc_compressive_cluster (Section 2.2, step 2).
+struct CompressiveState {
+  DevBuf s;                     // double [n]: row energies |theta_i|^2
+  DevBuf q, prefix;             // int64 [n]: quantised weights and their inclusive prefix sums
+  DevBuf flags, pos;            // int32 [n]: drawn-node flags and their inclusive prefix sums
+  DevBuf sums;                  // chunk totals of the scans
+  DevBuf omega;                 // int32 [min(n, draws)]: sampled nodes in increasing order
+  DevBuf smax;                  // uint64: bits of max_i s_i
+  DevBuf yo;                    // [n_omega][d]: rows of the sampled nodes
+  DevBuf labels;                // int32 [restarts][n_omega]: reduced assignment of each restart
+  DevBuf z, x;                  // float [n][k] right-hand side, float [n][cpad] interpolation
+  DevBuf assign;                // int32 [n]
+  DevBuf theta_stage, y_stage;  // caller features staged from host memory
+};
+// Row energies, integer weights and prefix sums, the draws and the sorted sample; the
+// sample size is pos[n - 1] and the weight total prefix[n - 1] (device).
+cudaError_t compressive_sample(CompressiveState& cs, const float* theta, int64_t ld, int64_t n, int d,
+                               int64_t n_draws, uint64_t seed, cudaStream_t s);
+// out[r] = y[omega[r]] for r < no (n_omega x d, leading dimension d, dtype of y).
+cudaError_t compressive_gather(const void* y, int y_dtype, int64_t ldy, const int32_t* omega, int64_t no, int d,
+                               void* out, cudaStream_t s);
+// z[omega[r]][labels[r]] = T / (n q) for the sampled nodes (z zeroed by the caller).
+cudaError_t compressive_rhs(const CompressiveState& cs, const int32_t* labels, int64_t no, int64_t n, float* z,
+                            int64_t ldz, cudaStream_t s);
+// out[i] = lowest index of the maximum of row i of x (k columns).
+cudaError_t compressive_argmax(const float* x, int64_t ldx, int64_t n, int k, int32_t* out, cudaStream_t s);
+void compressive_release(CompressiveState& cs);
+
 // ------------------------------------------------------------------ k-means (kmeans.cu)
 
 struct KmeansState {
@@ -286,6 +316,7 @@ struct csc_ctx {
   csc::DevBuf b_waves;  // int64 [waves]: end of each wave in the item list
   csc::GradState gs;    // differentiation: checkpoints of the last csc_filter_forward
   csc::DevBuf sim;      // csc_laplacian_distance scratch: double [2n + 2 grid + 8]
+  csc::CompressiveState cmp;  // csc_compressive_cluster scratch
   csc::DevBuf b_work;   // uint64 claim counter, int64 [waves] claim ends, uint32 [tiles][m + 1] done counts
   cudaStream_t b_cap = nullptr;
   cudaGraphExec_t b_exec = nullptr;
