@@ -50,6 +50,7 @@ def args_parse():
     ap.add_argument("--tile", type=int, default=0, help="column-tile width (0 = library default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-grad", action="store_true", help="skip the differentiation timing")
+    ap.add_argument("--no-compressive", action="store_true", help="skip the compressive k-means timing")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
     return a
@@ -306,6 +307,41 @@ def differentiation_timing(seed=4, reps=3):
             "unit": UNIT}
 
 
+def compressive_timing(ctx, full_assign, seed=11, reps=3):
+    """Compressive k-means (sampled k-means + k interpolating filterings) on the context's
+    last snapshot, against the full k-means assignment of the same features."""
+    import numpy as np
+    import torch
+    from scipy.optimize import linear_sum_assignment
+
+    full = full_assign.cpu().numpy()
+    out = torch.zeros(N_NODES, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for label, draws in (("default", 0), ("4x", int(np.ceil(8 * K_CLUST * np.log(K_CLUST))))):
+        ctx.compressive_cluster(K_CLUST, n_draws=draws, seed=seed, assign_out=out)  # warm-up
+        st0 = ctx.stats()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            r = ctx.compressive_cluster(K_CLUST, n_draws=draws, seed=seed, assign_out=out)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        st1 = ctx.stats()
+        got = out.cpu().numpy()
+        c = np.zeros((K_CLUST, K_CLUST))
+        np.add.at(c, (got, full), 1)
+        ri, ci = linear_sum_assignment(-c)
+        res[label] = {"n_draws": draws or int(np.ceil(2 * K_CLUST * np.log(K_CLUST))),
+                      "n_sampled": r["n_sampled"], "ms": ev[0].elapsed_time(ev[1]) / reps,
+                      "interpolation_step_ms": (st1["step_ms"] - st0["step_ms"]) / reps,
+                      "agreement_with_full_kmeans": float(c[ri, ci].sum() / N_NODES)}
+    return {"workload": "last timed snapshot of the bench sequence: k=100 clusters, 10 restarts of the "
+                        "reduced k-means, interpolation by the order-100 low pass of the features",
+            **res}
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return 0
@@ -409,6 +445,9 @@ def run_ours(a, rank, world, local):
     ms, units, info, clk, phases = run_sequence(ctx, dev_graphs, assign, a.warmup)
     stats = ctx.stats()
     tile = int(stats["tile"])
+    comp = None
+    if rank == 0 and not a.no_compressive:
+        comp = compressive_timing(ctx, assign)
     ctx.close()
     ms_max = dist.reduce(ms, "max")
     units_all = dist.reduce(units, "sum")
@@ -466,6 +505,7 @@ def run_ours(a, rank, world, local):
         "gpu_launches": stats["launches"],
         "batched_vs_plain": batched,
         "differentiation": grad,
+        "compressive_kmeans": comp,
         "phase_ms": phases,
         "per_step": {"lambda": [i["lam"] for i in info], "evals": [i["evals"] for i in info],
                      "kmeans_iters": [i["iters"] for i in info]},
