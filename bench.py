@@ -307,12 +307,19 @@ def differentiation_timing(seed=4, reps=3):
             "unit": UNIT}
 
 
-def compressive_timing(ctx, full_assign, seed=11, reps=3):
+def compressive_timing(ctx, full_assign, planted, seed=11, reps=3):
     """Compressive k-means (sampled k-means + k interpolating filterings) on the context's
-    last snapshot, against the full k-means assignment of the same features."""
+    last snapshot, against the full k-means assignment of the same features and against the
+    planted blocks of the generator."""
     import numpy as np
     import torch
     from scipy.optimize import linear_sum_assignment
+
+    def agreement(a, b):
+        c = np.zeros((K_CLUST, K_CLUST))
+        np.add.at(c, (a, b), 1)
+        ri, ci = linear_sum_assignment(-c)
+        return float(c[ri, ci].sum() / a.size)
 
     full = full_assign.cpu().numpy()
     out = torch.zeros(N_NODES, dtype=torch.int32, device="cuda")
@@ -330,16 +337,14 @@ def compressive_timing(ctx, full_assign, seed=11, reps=3):
         torch.cuda.synchronize()
         st1 = ctx.stats()
         got = out.cpu().numpy()
-        c = np.zeros((K_CLUST, K_CLUST))
-        np.add.at(c, (got, full), 1)
-        ri, ci = linear_sum_assignment(-c)
         res[label] = {"n_draws": draws or int(np.ceil(2 * K_CLUST * np.log(K_CLUST))),
                       "n_sampled": r["n_sampled"], "ms": ev[0].elapsed_time(ev[1]) / reps,
                       "interpolation_step_ms": (st1["step_ms"] - st0["step_ms"]) / reps,
-                      "agreement_with_full_kmeans": float(c[ri, ci].sum() / N_NODES)}
+                      "agreement_with_full_kmeans": agreement(got, full),
+                      "agreement_with_planted": agreement(got, planted)}
     return {"workload": "last timed snapshot of the bench sequence: k=100 clusters, 10 restarts of the "
                         "reduced k-means, interpolation by the order-100 low pass of the features",
-            **res}
+            "full_kmeans_agreement_with_planted": agreement(full, planted), **res}
 
 
 def run_reference(a, rank, world):
@@ -447,7 +452,7 @@ def run_ours(a, rank, world, local):
     tile = int(stats["tile"])
     comp = None
     if rank == 0 and not a.no_compressive:
-        comp = compressive_timing(ctx, assign)
+        comp = compressive_timing(ctx, assign, np.asarray(snaps[-1].labels))
     ctx.close()
     ms_max = dist.reduce(ms, "max")
     units_all = dist.reduce(units, "sum")

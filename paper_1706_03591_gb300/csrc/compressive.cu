@@ -25,21 +25,59 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;  // elements per block of the first scan level
 
-// One thread per row: the float64 sum of squares in column order, and the running maximum
-// (non-negative doubles order like their bit patterns).
-__global__ void row_energy_kernel(const float* __restrict__ theta, int64_t ld, int64_t n, int d,
-                                  double* __restrict__ s, unsigned long long* __restrict__ smax_bits) {
+// Float64 sum of squares of each row in column order, and the running maximum
+// (non-negative doubles order like their bit patterns).  A block owns 256 rows and walks
+// the columns in chunks of 32: the chunk is staged in shared memory with coalesced 16-byte
+// loads (a padded row stride keeps the column reads conflict-free), then each thread adds
+// its row's 32 squares in order, so the sum is the same as a plain left-to-right loop.
+constexpr int kEnergyRows = 256;
+constexpr int kEnergyCols = 32;
+
+__global__ void __launch_bounds__(kEnergyRows) row_energy_kernel(const float* __restrict__ theta, int64_t ld,
+                                                                 int64_t n, int d, double* __restrict__ s,
+                                                                 unsigned long long* __restrict__ smax_bits) {
+  __shared__ float tile[kEnergyRows][kEnergyCols + 1];
+  const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(theta) % 16) == 0;
   double mx = 0.0;
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    const float* r = theta + row * ld;
+  for (int64_t r0 = (int64_t)blockIdx.x * kEnergyRows; r0 < n; r0 += (int64_t)gridDim.x * kEnergyRows) {
     double acc = 0.0;
-    for (int l = 0; l < d; ++l) {
-      const double v = (double)r[l];
-      acc = fma(v, v, acc);  // v * v is exact, so this is the rounded sum acc + v^2
+    for (int c0 = 0; c0 < d; c0 += kEnergyCols) {
+      // 256 rows x 32 columns: thread t loads column group t % 8 of rows t / 8 + 32 i
+      const int cg = threadIdx.x & 7;
+      for (int i = 0; i < kEnergyRows / 32; ++i) {
+        const int rl = (threadIdx.x >> 3) + 32 * i;
+        const int64_t row = r0 + rl;
+        const int col = c0 + cg * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < n) {
+          const float* src = theta + row * ld + col;
+          if (vec && col + 4 <= d) {
+            v = *reinterpret_cast<const float4*>(src);
+          } else {
+            if (col < d) v.x = src[0];
+            if (col + 1 < d) v.y = src[1];
+            if (col + 2 < d) v.z = src[2];
+            if (col + 3 < d) v.w = src[3];
+          }
+        }
+        tile[rl][cg * 4] = v.x;
+        tile[rl][cg * 4 + 1] = v.y;
+        tile[rl][cg * 4 + 2] = v.z;
+        tile[rl][cg * 4 + 3] = v.w;
+      }
+      __syncthreads();
+      const int cols = min(kEnergyCols, d - c0);
+      for (int l = 0; l < cols; ++l) {
+        const double v = (double)tile[threadIdx.x][l];
+        acc = fma(v, v, acc);  // v * v is exact, so this is the rounded sum acc + v^2
+      }
+      __syncthreads();
     }
-    s[row] = acc;
-    mx = fmax(mx, acc);
+    const int64_t row = r0 + threadIdx.x;
+    if (row < n) {
+      s[row] = acc;
+      mx = fmax(mx, acc);
+    }
   }
   for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   if ((threadIdx.x & 31) == 0) atomicMax(smax_bits, (unsigned long long)__double_as_longlong(mx));
@@ -187,17 +225,25 @@ __global__ void build_rhs_kernel(const int32_t* __restrict__ omega, const int32_
   }
 }
 
-// Lowest column index of each row maximum.
+// Lowest column index of each row maximum, one warp per row (coalesced row reads, then a
+// shuffle reduction that prefers the larger value and, among equal values, the lower index).
 __global__ void argmax_kernel(const float* __restrict__ x, int64_t ldx, int64_t n, int k, int32_t* __restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const float* r = x + i * ldx;
-    float best = r[0];
-    int bi = 0;
-    for (int j = 1; j < k; ++j) {
+    float best = -INFINITY;
+    int bi = k;
+    for (int j = lane; j < k; j += 32) {
       const float v = r[j];
-      if (v > best) { best = v; bi = j; }
+      if (v > best || bi == k) { best = v; bi = j; }
     }
-    out[i] = bi;
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (oi < k && (bi == k || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+    }
+    if (lane == 0) out[i] = bi;
   }
 }
 
@@ -214,7 +260,8 @@ cudaError_t compressive_sample(CompressiveState& cs, const float* theta, int64_t
   cudaError_t e = cudaMemsetAsync(cs.smax.ptr, 0, 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(cs.flags.ptr, 0, (size_t)n * 4, s);
   if (e != cudaSuccess) return e;
-  row_energy_kernel<<<grid, 256, 0, s>>>(theta, ld, n, d, as<double>(cs.s), as<unsigned long long>(cs.smax));
+  row_energy_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms() * 4, (n + kEnergyRows - 1) / kEnergyRows)),
+                      kEnergyRows, 0, s>>>(theta, ld, n, d, as<double>(cs.s), as<unsigned long long>(cs.smax));
   int lg_n = 0;
   while ((int64_t(1) << lg_n) < std::max<int64_t>(n, 2)) ++lg_n;
   quantise_kernel<<<grid, 256, 0, s>>>(as<double>(cs.s), n, lg_n, as<unsigned long long>(cs.smax),
