@@ -228,6 +228,9 @@ struct KmeansState {
   DevBuf csplit, cn2t;          // bfloat16 [2][npad][dp] (c0, c1), float [npad] |c|^2
   DevBuf masks;                 // uint16 [n][npad / 16] candidate masks of near-tie rows
   alignas(64) unsigned char tmaps[3][128];  // TMA maps of y0, y1 and (c0, c1)
+  unsigned long long* hist_host = nullptr;   // pinned [passes][5]: counters of each pass
+  size_t hist_cap = 0;
+  cudaEvent_t pass_ev[2] = {nullptr, nullptr};  // completion of a pass's counter copy
 };
 
 // Shape of the tensor-core distance pass for (n, k, d, dtype); ok = false when k or d

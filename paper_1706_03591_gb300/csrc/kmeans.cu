@@ -1020,34 +1020,67 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   CK(finalize());
 
   if (use_tc) {
-    // tensor-core distance pass on every row each pass; near ties decided in float64
+    // Tensor-core distance pass on every row each pass; near ties decided in float64.  The
+    // host queues pass it before it reads the counters of pass it - 1 (copied to pinned
+    // memory), so the GPU does not wait for the host between passes.  The update after pass
+    // it is either the full recomputation or the incremental one from the moved rows; both
+    // give the same integer sums, and the choice (full after the first pass and whenever the
+    // previous pass moved more than n / 16 rows) only affects speed.  When pass j turns out
+    // to have converged, pass j + 1 is already queued: it finds no move and leaves the
+    // assignment, the sums and the centroids as they were, so the result is the one at j.
+    if (st.hist_cap < (size_t)max_iter * 5) {
+      if (st.hist_host) cudaFreeHost(st.hist_host);
+      st.hist_host = nullptr;
+      st.hist_cap = 0;
+      CK(cudaHostAlloc(reinterpret_cast<void**>(&st.hist_host), (size_t)max_iter * 5 * 8, cudaHostAllocDefault));
+      st.hist_cap = (size_t)max_iter * 5;
+    }
+    for (cudaEvent_t& e : st.pass_ev)
+      if (e == nullptr) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CK(cudaMemsetAsync(counters + 4, 0, 8, s));
-    int it = 0;
+    int examined = 0, stop = 0;
+    unsigned long long last_moved = ~0ull;
     bool converged = false;
     int64_t decided = 0;
-    for (it = 1; it <= max_iter; ++it) {
-      CK(cudaMemsetAsync(counters, 0, 32, s));
-      TRACE("tc pass");
-      CK(kmeans_tc_pass(st, tp, y, y_dtype, n, d, ldy, k, it > 1, s));
-      launches += 3;
-      decided += n;
-      unsigned long long cnt[5] = {0, 0, 0, 0, 0};
-      CK(cudaMemcpyAsync(cnt, counters, 40, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+    // reads the counters of pass j (1-based) once its copy has completed
+    auto examine = [&](int j) -> csc_status {
+      cudaError_t e = cudaEventSynchronize(st.pass_ev[j & 1]);
+      if (e != cudaSuccess) {
+        if (err) *err = std::string("k-means: ") + cudaGetErrorString(e);
+        return CSC_ECUDA;
+      }
+      const unsigned long long* cnt = st.hist_host + (size_t)(j - 1) * 5;
       if (cnt[4] != 0) {
         if (err) *err = "k-means: a bounded wait in the tensor-core pass expired (code " +
                         std::to_string(cnt[4]) + ")";
         return CSC_ETIMEOUT;
       }
-      const unsigned long long changed = cnt[0];
       res->near_ties += (int64_t)cnt[1];
+      decided += n;
+      examined = j;
+      last_moved = j == 1 ? ~0ull : cnt[0];  // the first pass does not record moves
       if (debug_on()) {
-        fprintf(stderr, "[csc] kmeans tc pass %d: near ties %llu moved %llu\n", it, cnt[1], changed);
+        fprintf(stderr, "[csc] kmeans tc pass %d: near ties %llu moved %llu\n", j, cnt[1], cnt[0]);
         fflush(stderr);
       }
-      converged = it > 1 && changed == 0;
-      if (converged || it == max_iter) break;
-      if (it == 1 || changed > (unsigned long long)(n / 16)) {
+      if (j > 1 && cnt[0] == 0) converged = true;
+      return CSC_OK;
+    };
+    for (int it = 1; it <= max_iter; ++it) {
+      CK(cudaMemsetAsync(counters, 0, 32, s));
+      TRACE("tc pass");
+      CK(kmeans_tc_pass(st, tp, y, y_dtype, n, d, ldy, k, it > 1, s));
+      launches += 3;
+      CK(cudaMemcpyAsync(st.hist_host + (size_t)(it - 1) * 5, counters, 40, cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(st.pass_ev[it & 1], s));
+      stop = it;
+      if (it > 1) {
+        const csc_status cs = examine(it - 1);
+        if (cs != CSC_OK) return cs;
+        if (converged) break;
+      }
+      if (it == max_iter) break;
+      if (it == 1 || last_moved > (unsigned long long)(n / 16)) {
         CK(accumulate(as<int32_t>(st.assign)));
       } else {
         move_kernel<TY><<<sms * 4, 256, 0, s>>>(y, ldy, n, d, as<int32_t>(st.moved), counters, scale,
@@ -1057,8 +1090,11 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
       }
       CK(finalize());
     }
-    if (it > max_iter) it = max_iter;
-    res->iters = it;
+    if (!converged) {
+      const csc_status cs = examine(stop);
+      if (cs != CSC_OK) return cs;
+    }
+    res->iters = examined;
     res->converged = converged;
     res->decided = decided;
   }
@@ -1195,6 +1231,13 @@ void kmeans_release(KmeansState& st) {
   for (DevBuf* b : all) release(*b);
   release(st.perm);
   release(st.hist);
+  if (st.hist_host) cudaFreeHost(st.hist_host);
+  st.hist_host = nullptr;
+  st.hist_cap = 0;
+  for (cudaEvent_t& e : st.pass_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   kmeans_tc_release(st);
 }
 
