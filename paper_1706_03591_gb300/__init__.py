@@ -49,12 +49,32 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+# element types each array argument may have (numpy has no bfloat16: host features are float32)
+_DTYPES = {
+    "row_ptr": ("int64",), "col_idx": ("int32",), "vals": ("float32",),
+    "assign_out": ("int32",), "prev_assign": ("int32",),
+    "psi_out": ("float32",), "theta": ("float32",), "interp_out": ("float32",),
+    "R": ("float32", "bfloat16"), "Y": ("float32", "bfloat16"),
+    "out": ("float32", "bfloat16"), "dst": ("float32", "bfloat16"),
+}
+
+
+def _check_dtype(x, kind: str):
+    want = _DTYPES.get(kind)
+    if want is None:
+        return
+    name = str(x.dtype).replace("torch.", "")
+    if name not in want:
+        raise TypeError(f"{kind}: element type {name}, expected {' or '.join(want)}")
+
+
 def _arr(x, kind: str):
     """(pointer, where, dtype-code, leading dimension) of a 1-D/2-D array argument."""
     if x is None:
         return None, _abi.CSC_HOST, _abi.CSC_F32, 0
     if _is_torch(x):
         import torch
+        _check_dtype(x, kind)
         if x.numel() > 1 and (x.dim() == 2 and x.stride(1) != 1 or x.dim() == 1 and x.stride(0) != 1):
             raise ValueError(f"{kind}: innermost dimension must be contiguous")
         where = _abi.CSC_DEVICE if x.is_cuda else _abi.CSC_HOST
@@ -62,6 +82,7 @@ def _arr(x, kind: str):
         ld = x.stride(0) if x.dim() == 2 else 0
         return C.c_void_p(x.data_ptr()), where, code, ld
     a = np.asarray(x)
+    _check_dtype(a, kind)
     if a.size > 1 and (a.ndim == 2 and a.strides[1] != a.itemsize
                        or a.ndim == 1 and a.strides[0] != a.itemsize):
         raise ValueError(f"{kind}: innermost dimension must be contiguous")

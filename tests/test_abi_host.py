@@ -99,3 +99,22 @@ def test_lambda_search_cap_and_bad_args(lib):
         lib.csc_lambda_search_moments(m, mu, 8, 8, 0, 0.5, -1.0, 7)
     with pytest.raises(lib.CscError):
         lib.csc_filter_coeffs(-1, 0.5)
+
+
+def test_binding_rejects_wrong_element_types():
+    """Array arguments are passed as raw pointers, so the binding checks their element types
+    before any call: a float64 feature block or an int64 assignment buffer is refused."""
+    import paper_1706_03591_gb300 as csc
+    with pytest.raises(TypeError, match="theta"):
+        csc._arr(np.zeros((4, 3)), "theta")
+    with pytest.raises(TypeError, match="assign_out"):
+        csc._arr(np.zeros(4, dtype=np.int64), "assign_out")
+    with pytest.raises(TypeError, match="col_idx"):
+        csc._arr(np.zeros(4, dtype=np.int64), "col_idx")
+    ptr, where, code, ld = csc._arr(np.zeros((4, 3), dtype=np.float32), "Y")
+    assert where == csc.CSC_HOST and code == csc.CSC_F32 and ld == 3
+    torch = pytest.importorskip("torch")
+    _, _, code, _ = csc._arr(torch.zeros((4, 3), dtype=torch.bfloat16), "Y")
+    assert code == csc.CSC_BF16
+    with pytest.raises(TypeError, match="psi_out"):
+        csc._arr(torch.zeros((4, 3), dtype=torch.bfloat16), "psi_out")
