@@ -252,6 +252,12 @@ def csc_filter_batched(h, graphs, m: int, want_moments: bool = True):
     psi (device float32 tensor n x c or None).  Returns the moments, shape (len(graphs), 2m+1)."""
     descs = (_abi.csc_graph_desc * len(graphs))()
     for i, g in enumerate(graphs):
+        for key in ("row_ptr", "col_idx", "vals", "psi"):
+            x = g.get(key)
+            if x is not None:
+                if not (_is_torch(x) and x.is_cuda):
+                    raise ValueError(f"graph {i}: {key} must be a CUDA tensor")
+                _check_dtype(x, "psi_out" if key == "psi" else key)
         dsc = descs[i]
         dsc.n = int(g["n"])
         dsc.nnz = int(g["col_idx"].numel())
