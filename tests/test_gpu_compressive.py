@@ -83,6 +83,42 @@ def test_compressive_parity_small(gpu_lib, y_dtype):
     _check_assign(assign, ref["x"])
 
 
+def test_compressive_parity_weighted_with_isolated_nodes(gpu_lib):
+    """Symmetric random weights and three isolated nodes (their L~ rows are zero, so the
+    interpolation there is h(1) z): same sample, restart, labels and interpolation."""
+    n, k, d, m = 2500, 5, 40, 40
+    g = W.sbm_graph(n, k, 25, 20, seed=9)
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    iso = np.array([3, 700, 2499])
+    keep = ~np.isin(rows, iso) & ~np.isin(g.col_idx, iso)
+    rows, cols = rows[keep], g.col_idx[keep].astype(np.int32)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, rows + 1, 1)
+    rp = np.cumsum(rp)
+    key = np.minimum(rows, cols).astype(np.int64) * n + np.maximum(rows, cols)
+    _, inv = np.unique(key, return_inverse=True)
+    vals = np.random.default_rng(2).uniform(0.5, 2.0, inv.max() + 1)[inv].astype(np.float32)
+    lt = lp.shifted_laplacian(n, rp, cols, vals)
+    lam = 0.35
+    r = W.gaussian_block(n, d, d, seed=12).astype(np.float64)
+    theta = cb.cheb_filter(lt, r, m, lam).astype(np.float32)
+    y = (theta / np.linalg.norm(theta, axis=1, keepdims=True)).astype(np.float32)
+    assign = np.zeros(n, dtype=np.int32)
+    x = np.zeros((n, k), dtype=np.float32)
+    with gpu_lib.Context() as ctx:
+        ctx.set_graph(n, dev(rp), dev(cols), dev(vals))
+        res = ctx.compressive_cluster(k, dev(theta), dev(y), n_draws=80, n_init=5, lambda_c=lam, m=m,
+                                      seed=21, assign_out=assign, want_sample=True, interp_out=x)
+    ref = ck.compressive_kmeans(n, rp, cols, vals, theta, y, k, 80, m, lam, 21, n_init=5)
+    np.testing.assert_array_equal(res["sample"], ref["omega"])
+    assert res["restart"] == ref["restart"]
+    np.testing.assert_array_equal(res["sample_labels"], ref["labels"])
+    err = rel(x, ref["x"])
+    print(f"weighted compressive interpolation: float32 error {err:.3e}")
+    assert err < FP32_TOL
+    _check_assign(assign, ref["x"])
+
+
 def test_compressive_on_context_features(gpu_lib):
     """After csc_filter, the call on the context's own features: same moments afterwards,
     and an assignment close to the full k-means of the same features."""
