@@ -1,6 +1,6 @@
 // Compressive k-means (Section 2.2, step 2; cost in Section 4.2): the device kernels of the
 // sampling, the reduced feature block, the interpolation right-hand side and the final
-// assignment.  The driver is csc_compressive_cluster in api.cu; the reduced k-means and the
+// assignment.  The host side is csc_compressive_cluster in api.cu; the reduced k-means and the
 // interpolation filter reuse the Lloyd and Chebyshev kernels.
 //
 // Sampling is exact integer work, so the sampled set does not depend on thread order:
