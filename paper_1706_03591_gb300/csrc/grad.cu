@@ -75,7 +75,7 @@ struct AdjArgs {
 
 // One reverse step: row-parallel, the LPR = w / 4 lanes of a slot own a row.
 template <int LPR>
-__global__ void __launch_bounds__(kBlk, 3) adjoint_step_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(kBlk, 4) adjoint_step_kernel(AdjArgs a) {
   constexpr int S = 32 / LPR;
   const int lane = threadIdx.x & 31;
   const int slot = lane / LPR, sub = lane % LPR;
