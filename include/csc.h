@@ -331,6 +331,24 @@ csc_status csc_laplacian_distance(csc_ctx* ctx, int64_t n, const int64_t* rp_a, 
                                   const float* val_a, const int64_t* rp_b, const int32_t* col_b,
                                   const float* val_b, double* rho_out);
 
+/* ---------------------------------------------------------------- checkpoint / resume */
+
+/* Algorithm 1 carries the feature ring Theta_{t-1}, the cutoff lambda_{t-1} and the
+ * assignment X_{t-1} from one snapshot to the next.  csc_save_state writes that state to a
+ * binary file at path: the ring (Theta float32 n x d and its row-normalised copy in the
+ * context's precision), the ring stamps, the snapshot counter, the next signal column id,
+ * the cutoff, the moments of the last filtering and the previous assignment with its k.
+ * csc_load_state reads it into a context created with the same precision, replacing that
+ * context's dynamic state; the graph is not part of the state, and the next csc_set_graph must
+ * have the saved n.  A resumed context continues the sequence exactly as the saving one
+ * would have: the same signal columns, slots, cutoff check and warm start.
+ * The file is written in the machine's byte order: magic "CSCSTATE", version 1.
+ * Errors: CSC_ESTATE (save before any csc_filter), CSC_EINVAL (NULL path, a file that cannot
+ * be opened, written or read, not a state file, a corrupt or truncated file, a precision
+ * mismatch), CSC_ENOMEM, CSC_ECUDA. */
+csc_status csc_save_state(csc_ctx* ctx, const char* path);
+csc_status csc_load_state(csc_ctx* ctx, const char* path);
+
 /* ---------------------------------------------------------------- compressive k-means */
 
 /* Compressive k-means (Section 2.2, step 2; cost counted in Section 4.2): k-means on a

@@ -22,7 +22,7 @@ __all__ = [
     "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
     "csc_filter_forward", "csc_filter_vjp", "csc_kmeans_loss_grad", "cheb_filter_layer",
-    "csc_laplacian_distance", "csc_compressive_cluster",
+    "csc_laplacian_distance", "csc_compressive_cluster", "csc_save_state", "csc_load_state",
 ]
 
 
@@ -341,6 +341,16 @@ def csc_laplacian_distance(h, n: int, graph_a, graph_b) -> float:
     return rho.value
 
 
+def csc_save_state(h, path: str) -> None:
+    """Writes the context's dynamic state (feature ring, cutoff, previous assignment) to path."""
+    _check(_lib().csc_save_state(h, str(path).encode()), h, "csc_save_state")
+
+
+def csc_load_state(h, path: str) -> None:
+    """Replaces the context's dynamic state with the one saved at path."""
+    _check(_lib().csc_load_state(h, str(path).encode()), h, "csc_load_state")
+
+
 def csc_compressive_cluster(h, k: int, theta=None, Y=None, n_draws: int = 0, n_init: int = 0,
                             lambda_c: float = -1.0, m: int = 0, seed: int = 0, max_iter: int = 0,
                             assign_out=None, want_sample: bool = False, interp_out=None):
@@ -485,6 +495,12 @@ class Context:
 
     def get_features(self, dst, normalized=False):
         csc_get_features(self.h, dst, normalized)
+
+    def save_state(self, path):
+        csc_save_state(self.h, path)
+
+    def load_state(self, path):
+        csc_load_state(self.h, path)
 
     def compressive_cluster(self, k, theta=None, Y=None, **kw):
         return csc_compressive_cluster(self.h, k, theta, Y, **kw)

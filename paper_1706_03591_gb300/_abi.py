@@ -93,6 +93,8 @@ SIGNATURES = {
     "csc_filter_vjp": (_i32, [_p, _p, _i64, _pd, _p]),
     "csc_kmeans_loss_grad": (_i32, [_p, _p, _i64, _i64, _i32, _p, _i32, _p, _p, _i64, _pd]),
     "csc_laplacian_distance": (_i32, [_p, _i64, _p, _p, _p, _p, _p, _p, _pd]),
+    "csc_save_state": (_i32, [_p, C.c_char_p]),
+    "csc_load_state": (_i32, [_p, C.c_char_p]),
     "csc_compressive_cluster": (_i32, [_p, _p, _p, _i32, _i32, _i64, _i32, _i32, _i64, _i32, _dbl, _i32, _u64,
                                        _i32, _p, _i32, _p, _p, _p, _i64, C.POINTER(C.c_int64), _pi]),
 }

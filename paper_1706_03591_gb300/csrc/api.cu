@@ -350,6 +350,25 @@ csc_status copy_out(csc_ctx* ctx, const void* src, int src_dtype, int64_t ld_src
 
 }  // namespace
 
+// ------------------------------------------------------------------ checkpoint / resume file
+
+namespace {
+
+constexpr char kStateMagic[8] = {'C', 'S', 'C', 'S', 'T', 'A', 'T', 'E'};
+constexpr uint32_t kStateVersion = 1;
+
+struct StateFile {
+  FILE* f = nullptr;
+  ~StateFile() {
+    if (f) fclose(f);
+  }
+};
+
+bool put(FILE* f, const void* p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
+bool get(FILE* f, void* p, size_t bytes) { return bytes == 0 || fread(p, 1, bytes, f) == bytes; }
+
+}  // namespace
+
 extern "C" {
 
 void csc_default_opts(csc_opts* o) {
@@ -636,6 +655,8 @@ csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k
   const int64_t n = ctx->g.n;
   if (ctx->t > 0 && d != ctx->ring_d)
     return fail(ctx, CSC_EINVAL, "csc_filter: d must stay the same across snapshots");
+  if (ctx->t > 0 && n != ctx->ring_n)
+    return fail(ctx, CSC_ESTATE, "csc_filter: the graph's n differs from the feature ring's");
   if (lambda_c < 0 && !ctx->has_lambda && k < 1)
     return fail(ctx, CSC_ESTATE, "csc_filter: no cutoff yet; pass lambda_c >= 0 or k >= 1");
   cudaStream_t s = ctx->stream;
@@ -948,6 +969,106 @@ csc_status csc_compressive_cluster(csc_ctx* ctx, const float* theta, const void*
   CUDA_OK(cudaStreamSynchronize(s));
   if (n_sampled_out) *n_sampled_out = n_omega;
   if (restart_out) *restart_out = pick;
+  return CSC_OK;
+}
+
+
+csc_status csc_save_state(csc_ctx* ctx, const char* path) {
+  if (!ctx) return CSC_EINVAL;
+  if (!path) return fail(ctx, CSC_EINVAL, "csc_save_state: null path");
+  if (ctx->t == 0) return fail(ctx, CSC_ESTATE, "csc_save_state: nothing filtered yet");
+  const int64_t n = ctx->ring_n;
+  const int d = ctx->ring_d;
+  const size_t cells = (size_t)n * d;
+  const size_t ysz = dtype_size(ctx->opts.precision);
+  std::vector<float> theta(cells);
+  std::vector<unsigned char> y(cells * ysz);
+  std::vector<int32_t> prev;
+  cudaStream_t s = ctx->stream;
+  CUDA_OK(cudaMemcpyAsync(theta.data(), ctx->theta.ptr, cells * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaMemcpyAsync(y.data(), ctx->y.ptr, cells * ysz, cudaMemcpyDeviceToHost, s));
+  if (ctx->has_prev) {
+    prev.resize((size_t)n);
+    CUDA_OK(cudaMemcpyAsync(prev.data(), ctx->prev_assign.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_OK(cudaStreamSynchronize(s));
+  StateFile sf;
+  sf.f = fopen(path, "wb");
+  if (!sf.f) return fail(ctx, CSC_EINVAL, std::string("csc_save_state: cannot open ") + path);
+  const int32_t precision = ctx->opts.precision, ring_d = d, has_lambda = ctx->has_lambda ? 1 : 0;
+  const int32_t last_m = ctx->last_m, n_mu = (int32_t)ctx->mu.size();
+  const int32_t has_prev = ctx->has_prev ? 1 : 0, prev_k = ctx->prev_k;
+  const int64_t t = ctx->t, next_id = ctx->next_id;
+  const bool ok = put(sf.f, kStateMagic, 8) && put(sf.f, &kStateVersion, 4) && put(sf.f, &precision, 4) &&
+                  put(sf.f, &n, 8) && put(sf.f, &ring_d, 4) && put(sf.f, &t, 8) && put(sf.f, &next_id, 8) &&
+                  put(sf.f, &has_lambda, 4) && put(sf.f, &ctx->lambda, 8) && put(sf.f, &last_m, 4) &&
+                  put(sf.f, &n_mu, 4) && put(sf.f, ctx->mu.data(), ctx->mu.size() * 8) &&
+                  put(sf.f, ctx->stamp.data(), ctx->stamp.size() * 8) && put(sf.f, &has_prev, 4) &&
+                  put(sf.f, &prev_k, 4) && put(sf.f, theta.data(), cells * 4) && put(sf.f, y.data(), y.size()) &&
+                  put(sf.f, prev.data(), prev.size() * 4);
+  const bool closed = fclose(sf.f) == 0;
+  sf.f = nullptr;
+  if (!ok || !closed) return fail(ctx, CSC_EINVAL, std::string("csc_save_state: write failed for ") + path);
+  return CSC_OK;
+}
+
+csc_status csc_load_state(csc_ctx* ctx, const char* path) {
+  if (!ctx) return CSC_EINVAL;
+  if (!path) return fail(ctx, CSC_EINVAL, "csc_load_state: null path");
+  StateFile sf;
+  sf.f = fopen(path, "rb");
+  if (!sf.f) return fail(ctx, CSC_EINVAL, std::string("csc_load_state: cannot open ") + path);
+  char magic[8];
+  uint32_t version = 0;
+  int32_t precision = 0, ring_d = 0, has_lambda = 0, last_m = 0, n_mu = 0, has_prev = 0, prev_k = 0;
+  int64_t n = 0, t = 0, next_id = 0;
+  double lambda = 0.0;
+  if (!get(sf.f, magic, 8) || std::memcmp(magic, kStateMagic, 8) != 0 || !get(sf.f, &version, 4) ||
+      version != kStateVersion)
+    return fail(ctx, CSC_EINVAL, std::string("csc_load_state: not a state file: ") + path);
+  bool ok = get(sf.f, &precision, 4) && get(sf.f, &n, 8) && get(sf.f, &ring_d, 4) && get(sf.f, &t, 8) &&
+            get(sf.f, &next_id, 8) && get(sf.f, &has_lambda, 4) && get(sf.f, &lambda, 8) &&
+            get(sf.f, &last_m, 4) && get(sf.f, &n_mu, 4);
+  if (!ok || n < 1 || ring_d < 1 || ring_d > 1024 || t < 1 || next_id < 0 || n_mu < 0 || n_mu > (1 << 20) ||
+      !valid_dtype(precision))
+    return fail(ctx, CSC_EINVAL, "csc_load_state: corrupt header");
+  if (precision != ctx->opts.precision)
+    return fail(ctx, CSC_EINVAL, "csc_load_state: the state was saved with another precision");
+  std::vector<double> mu((size_t)n_mu);
+  std::vector<int64_t> stamp((size_t)ring_d);
+  ok = get(sf.f, mu.data(), mu.size() * 8) && get(sf.f, stamp.data(), stamp.size() * 8) &&
+       get(sf.f, &has_prev, 4) && get(sf.f, &prev_k, 4);
+  if (!ok || (has_prev != 0 && has_prev != 1) || (has_prev && prev_k < 1))
+    return fail(ctx, CSC_EINVAL, "csc_load_state: corrupt header");
+  const size_t cells = (size_t)n * ring_d;
+  const size_t ysz = dtype_size(precision);
+  std::vector<float> theta(cells);
+  std::vector<unsigned char> y(cells * ysz);
+  std::vector<int32_t> prev(has_prev ? (size_t)n : 0);
+  ok = get(sf.f, theta.data(), cells * 4) && get(sf.f, y.data(), y.size()) && get(sf.f, prev.data(), prev.size() * 4);
+  if (!ok) return fail(ctx, CSC_EINVAL, "csc_load_state: truncated file");
+  for (int32_t v : prev)
+    if (v < 0 || v >= prev_k) return fail(ctx, CSC_EINVAL, "csc_load_state: assignment label out of range");
+  cudaStream_t s = ctx->stream;
+  ALLOC_OK(csc::ensure(ctx->theta, cells * 4));
+  ALLOC_OK(csc::ensure(ctx->y, cells * 4));
+  ALLOC_OK(csc::ensure(ctx->slot_src, (size_t)ring_d * 4));
+  if (has_prev) ALLOC_OK(csc::ensure(ctx->prev_assign, (size_t)n * 4));
+  CUDA_OK(cudaMemcpyAsync(ctx->theta.ptr, theta.data(), cells * 4, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemcpyAsync(ctx->y.ptr, y.data(), y.size(), cudaMemcpyHostToDevice, s));
+  if (has_prev) CUDA_OK(cudaMemcpyAsync(ctx->prev_assign.ptr, prev.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  ctx->ring_n = n;
+  ctx->ring_d = ring_d;
+  ctx->t = t;
+  ctx->next_id = next_id;
+  ctx->has_lambda = has_lambda != 0;
+  ctx->lambda = lambda;
+  ctx->last_m = last_m;
+  ctx->mu = mu;
+  ctx->stamp = stamp;
+  ctx->has_prev = has_prev != 0;
+  ctx->prev_k = prev_k;
   return CSC_OK;
 }
 
