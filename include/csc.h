@@ -71,6 +71,9 @@ typedef struct csc_opts {
   int checked;      /* nonzero: validate the CSR on csc_set_graph (device input too) */
   int timing;       /* nonzero: time the Chebyshev step launches with CUDA events on the
                        context stream (read with csc_get_stats) */
+  int estimator;    /* eigencount of the cutoff search: 0 = (d/c) ||h(L) R||_F^2, which
+                       estimates tr h(L)^2 (default); 1 = (d/c) tr(R^T h(L) R), which
+                       estimates tr h(L) (Hutchinson) */
 } csc_opts;
 
 /* Counters of a context (csc_get_stats). */
@@ -142,6 +145,12 @@ double csc_count_tolerance(int k, int c);
  * = (d/c) ||h(L) R||_F^2 for c signals of variance 1/d. */
 csc_status csc_count_from_moments(int m, const double* mu, double lambda_c, int d, int c,
                                   double* count_out);
+
+/* The Hutchinson-type eigencount from the same moments: count = (d/c) sum_j a_j mu_j
+ * = (d/c) tr(R^T h(L) R), an unbiased estimate of tr h(L) for c signals of variance 1/d
+ * (csc_opts.estimator = 1 selects it in csc_estimate_lambda_k and csc_filter). */
+csc_status csc_trace_count_from_moments(int m, const double* mu, double lambda_c, int d, int c,
+                                        double* count_out);
 
 /* Section 4.1 dichotomy of Algorithm 1 on the moment-based eigencount:
  * with lambda_prev < 0 bisect [0, 2]; else test lambda_prev, then grow a bracket

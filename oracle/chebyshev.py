@@ -118,6 +118,13 @@ def eigencount(psi: np.ndarray, d: int) -> float:
     return float(d) / float(c) * float(np.sum(np.asarray(psi, dtype=np.float64) ** 2))
 
 
+def trace_count(r: np.ndarray, psi: np.ndarray, d: int) -> float:
+    """Hutchinson-type count (d/c) tr(R^T Psi~) = (d/c) tr(R^T h(L) R), an unbiased estimate
+    of tr h(L) for a block of c signals of variance 1/d (the alternative estimator)."""
+    c = psi.shape[1]
+    return float(d) / float(c) * float(np.sum(np.asarray(r, dtype=np.float64) * np.asarray(psi, dtype=np.float64)))
+
+
 def count_tolerance(k: int, c: int) -> float:
     """Acceptance half-width tau = max(0.5, 2 sqrt(2k/c))."""
     return max(0.5, 2.0 * math.sqrt(2.0 * k / c))

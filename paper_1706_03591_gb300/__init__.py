@@ -17,7 +17,7 @@ from ._abi import CSC_BF16, CSC_DEVICE, CSC_F32, CSC_HOST  # noqa: F401
 
 __all__ = [
     "CscError", "Context", "csc_create", "csc_destroy", "csc_last_error", "csc_set_graph",
-    "csc_filter_coeffs", "csc_count_tolerance", "csc_count_from_moments",
+    "csc_filter_coeffs", "csc_count_tolerance", "csc_count_from_moments", "csc_trace_count_from_moments",
     "csc_lambda_search_moments", "csc_signals", "csc_cheb_filter", "csc_kmeans",
     "csc_estimate_lambda_k", "csc_filter", "csc_get_features", "csc_get_moments", "csc_cluster",
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
@@ -156,6 +156,14 @@ def csc_count_from_moments(m: int, mu, lambda_c: float, d: int, c: int) -> float
     out = C.c_double()
     _check(_lib().csc_count_from_moments(m, mu.ctypes.data_as(C.POINTER(C.c_double)), lambda_c, d, c,
                                          C.byref(out)))
+    return out.value
+
+
+def csc_trace_count_from_moments(m: int, mu, lambda_c: float, d: int, c: int) -> float:
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    out = C.c_double()
+    _check(_lib().csc_trace_count_from_moments(m, mu.ctypes.data_as(C.POINTER(C.c_double)), lambda_c, d, c,
+                                               C.byref(out)))
     return out.value
 
 

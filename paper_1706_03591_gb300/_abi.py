@@ -24,6 +24,7 @@ class csc_opts(C.Structure):
         ("col_tile", C.c_int),
         ("checked", C.c_int),
         ("timing", C.c_int),
+        ("estimator", C.c_int),
     ]
 
 
@@ -76,6 +77,7 @@ SIGNATURES = {
     "csc_filter_coeffs": (_i32, [_i32, _dbl, _pd]),
     "csc_count_tolerance": (_dbl, [_i32, _i32]),
     "csc_count_from_moments": (_i32, [_i32, _pd, _dbl, _i32, _i32, _pd]),
+    "csc_trace_count_from_moments": (_i32, [_i32, _pd, _dbl, _i32, _i32, _pd]),
     "csc_lambda_search_moments": (_i32, [_i32, _pd, _i32, _i32, _i32, _dbl, _dbl, _i32, _pd, _pd, _pi]),
     "csc_signals": (_i32, [_p, _u64, _i64, _i64, _i32, _i32, _p, _i32, _i64, _i32]),
     "csc_cheb_filter": (_i32, [_p, _i32, _dbl, _p, _i32, _i32, _i64, _i32, _p, _i64, _i32, _pd]),

@@ -80,6 +80,13 @@ double count_moments(int m, const double* mu, const double* a, int d, int c) {
   return (double)d / (double)c * s;
 }
 
+// Hutchinson-type estimate (d/c) tr(R^T h(L) R) = (d/c) sum_j a_j mu_j of tr h(L).
+double count_moments_trace(int m, const double* mu, const double* a, int d, int c) {
+  double s = 0.0;
+  for (int j = 0; j <= m; ++j) s += a[j] * mu[j];
+  return (double)d / (double)c * s;
+}
+
 double tolerance(int k, int c) { return std::max(0.5, 2.0 * std::sqrt(2.0 * k / (double)c)); }
 
 // Dichotomy used by Algorithm 1 to refine the cutoff (Section 4.1; rule in csc.h).
@@ -304,6 +311,7 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
 double count_at(const csc_ctx* ctx, double lam, int d, int c) {
   std::vector<double> a(ctx->last_m + 1);
   coeffs(ctx->last_m, lam, a.data());
+  if (ctx->opts.estimator == 1) return count_moments_trace(ctx->last_m, ctx->mu.data(), a.data(), d, c);
   return count_moments(ctx->last_m, ctx->mu.data(), a.data(), d, c);
 }
 
@@ -380,6 +388,7 @@ void csc_default_opts(csc_opts* o) {
   o->col_tile = 0;
   o->checked = 0;
   o->timing = 0;
+  o->estimator = 0;
 }
 
 const char* csc_status_string(csc_status s) {
@@ -404,7 +413,7 @@ csc_status csc_create(csc_ctx** out, const csc_opts* opts, void* cuda_stream) {
   csc_default_opts(&o);
   if (opts) o = *opts;
   if (!valid_dtype(o.precision) || o.max_bisect < 1 || o.max_iter < 1 ||
-      (o.col_tile != 0 && !valid_tile(o.col_tile)))
+      (o.col_tile != 0 && !valid_tile(o.col_tile)) || (o.estimator != 0 && o.estimator != 1))
     return CSC_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -539,6 +548,15 @@ csc_status csc_count_from_moments(int m, const double* mu, double lambda_c, int 
   std::vector<double> a(m + 1);
   coeffs(m, lambda_c, a.data());
   *count_out = count_moments(m, mu, a.data(), d, c);
+  return CSC_OK;
+}
+
+csc_status csc_trace_count_from_moments(int m, const double* mu, double lambda_c, int d, int c,
+                                       double* count_out) {
+  if (m < 0 || !mu || d < 1 || c < 1 || !count_out) return CSC_EINVAL;
+  std::vector<double> a(m + 1);
+  coeffs(m, lambda_c, a.data());
+  *count_out = count_moments_trace(m, mu, a.data(), d, c);
   return CSC_OK;
 }
 

@@ -73,6 +73,13 @@ def test_count_from_moments_equals_direct_eigencount(lib):
         assert lib.csc_count_from_moments(m, mu, lam, d, c) == pytest.approx(direct, rel=1e-9)
 
 
+def test_trace_count_from_moments_equals_direct_trace_count(lib):
+    lt, r, mu, basis, d, c, m = _moments_case()
+    for lam in (0.2, 0.55, 0.9, 1.5):
+        direct = cb.trace_count(r, cb.combine(basis, cb.filter_coefficients(m, lam)), d)
+        assert lib.csc_trace_count_from_moments(m, mu, lam, d, c) == pytest.approx(direct, rel=1e-9)
+
+
 def test_lambda_search_matches_oracle_control_flow(lib):
     lt, r, mu, basis, d, c, m = _moments_case()
 

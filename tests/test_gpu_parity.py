@@ -196,6 +196,29 @@ def test_estimate_lambda_matches_oracle_dichotomy(gpu_lib, cfg1_graph):
     assert cnt == pytest.approx(cnt_ref, rel=1e-4)
 
 
+def test_estimate_lambda_with_the_trace_estimator(gpu_lib, cfg1_graph):
+    """csc_opts.estimator = 1: the dichotomy on the Hutchinson count (d/c) tr(R^T h(L) R)."""
+    g = cfg1_graph
+    k, m, d, seed = 10, 50, 64, 99
+    r = gaussian_columns(seed, g.n, np.arange(d), d)
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    basis = cb.cheb_basis(lt, r, m)
+
+    def count(lam):
+        return cb.trace_count(r, cb.combine(basis, cb.filter_coefficients(m, lam)), d)
+
+    lam_ref, cnt_ref, ev_ref = cb.lambda_search(count, k, cb.count_tolerance(k, d), None, 30)
+    with gpu_lib.Context({"estimator": 1}) as ctx:
+        upload_graph(ctx, g)
+        lam, cnt, ev = ctx.estimate_lambda_k(k, m, d, seed)
+    assert (lam, ev) == (lam_ref, ev_ref)
+    assert cnt == pytest.approx(cnt_ref, rel=1e-4)
+    with gpu_lib.Context() as ctx:
+        upload_graph(ctx, g)
+        lam0, _, _ = ctx.estimate_lambda_k(k, m, d, seed)
+    assert lam0 != lam        # the two estimators target different traces
+
+
 def _kmeans_case(n, d, k, seed, dtype=np.float32):
     y, _ = W.clustered_points(n, d, k, seed=seed, spread=0.6)
     return y.astype(dtype), W.forgy_indices(n, k, seed=seed + 1)

@@ -189,6 +189,24 @@ def test_eigencount_is_unbiased_for_trace_h_squared():
     assert abs(counts.mean() - target) < 4 * sem + 1e-9
 
 
+def test_trace_count_is_unbiased_for_trace_h():
+    """The alternative (Hutchinson) estimator (d/c) tr(R^T h(L) R) has mean tr h(L)."""
+    g, lt = _small_graph()
+    lam = np.linalg.eigvalsh(lp.normalized_laplacian_dense(g.n, g.row_ptr, g.col_idx))
+    m, lam_c, d = 40, 0.55, 16
+    a = cb.filter_coefficients(m, lam_c)
+    target = float(np.sum(cb.response(a, lam)))
+    counts = []
+    for seed in range(60):
+        r = W.gaussian_block(g.n, d, d, seed=2000 + seed).astype(np.float64)
+        counts.append(cb.trace_count(r, cb.cheb_filter(lt, r, m, lam_c), d))
+    counts = np.array(counts)
+    sem = counts.std(ddof=1) / math.sqrt(counts.size)
+    assert abs(counts.mean() - target) < 4 * sem + 1e-9
+    # the two estimators target different traces: tr h(L) > tr h(L)^2 when 0 < h < 1 somewhere
+    assert target > float(np.sum(cb.response(a, lam) ** 2))
+
+
 def test_count_monotone_in_cutoff():
     g, lt = _small_graph()
     r = W.gaussian_block(g.n, 8, 8, seed=4).astype(np.float64)
