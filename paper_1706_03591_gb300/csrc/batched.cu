@@ -9,6 +9,7 @@
 // that times the step kernel on the largest graph of each size class for the candidate tile
 // widths and keeps the fastest per class.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 
@@ -261,6 +262,12 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
       tiles_h.push_back(bt);
     }
   }
+  // Failure-detection test hook (host-side injection): with CSC_TEST_EXPIRE_WAIT set in the
+  // environment, the first tile waits for one more finished block than it has.  Its blocks are
+  // still bounded by the real item list, so nothing else changes: the bounded dependency wait
+  // runs out, every other wait sees the error word and leaves, and the call returns
+  // CSC_ETIMEOUT with the context usable for the next call.
+  if (!tiles_h.empty() && std::getenv("CSC_TEST_EXPIRE_WAIT") != nullptr) tiles_h[0].a.nblk += 1;
   B_CUDA(cudaMemcpyAsync(ctx->b_coef.ptr, coef_h.data(), coef_h.size() * 4, cudaMemcpyHostToDevice, s));
   B_CUDA(cudaMemcpyAsync(ctx->b_tiles.ptr, tiles_h.data(), tiles_h.size() * sizeof(csc::BatchTile),
                          cudaMemcpyHostToDevice, s));

@@ -151,3 +151,26 @@ def test_batched_weighted_edgeless_tiny_and_several_waves(gpu_lib):
         if g.n < 1000:
             mu_ref = cb.moments(lt, r, 2 * m)
             assert np.max(np.abs(mu[i] - mu_ref)) < FP32_TOL * mu_ref[0], i
+
+
+def test_expired_dependency_wait_returns_etimeout(gpu_lib, monkeypatch):
+    """Failure detection without a GPU fault: a host-side hook makes the first tile wait for a
+    block that does not exist.  The bounded wait runs out (about a second), the call returns
+    CSC_ETIMEOUT, and the same context then filters the batch correctly."""
+    import time
+    m = 20
+    batch = _batch(seed=5, count=4)
+    descs = _descs(batch)
+    with gpu_lib.Context({"precision": 1}) as ref_ctx:
+        mu_ref = ref_ctx.filter_batched(_descs(batch), m)
+    with gpu_lib.Context({"precision": 1}) as ctx:
+        monkeypatch.setenv("CSC_TEST_EXPIRE_WAIT", "1")
+        t0 = time.perf_counter()
+        with pytest.raises(gpu_lib.CscError) as e:
+            ctx.filter_batched(descs, m)
+        elapsed = time.perf_counter() - t0
+        monkeypatch.delenv("CSC_TEST_EXPIRE_WAIT")
+        assert e.value.status == 4 and "bounded dependency wait" in str(e.value)
+        assert elapsed < 60
+        mu = ctx.filter_batched(descs, m)
+    np.testing.assert_array_equal(mu, mu_ref)
