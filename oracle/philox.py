@@ -17,8 +17,9 @@ counter-based generator from its published definition:
 * Forgy indices: draw j uses counter (j, attempt, 0, 1); idx = floor(U n / 2^64)
   with U = x0 * 2^32 + x1; a repeated index is redrawn with attempt + 1.
 
-Parity: the generator is pinned by its statistics (mean, variance 1/d,
-normality, column independence), not by published known-answer vectors.
+Pins (tests/test_oracle_philox.py): the published known-answer vectors of
+Philox-4x32-10 (tests/golden/philox4x32_10_kat.txt), and the statistics of the
+signals (mean, variance 1/d, normality, column independence).
 """
 from __future__ import annotations
 

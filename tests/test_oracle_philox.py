@@ -1,4 +1,4 @@
-"""Statistical pins of the oracle's counter-based Gaussian signals (Section 2.2, approximate features)."""
+"""Pins of the oracle's counter-based generator and Gaussian signals (Section 2.2, approximate features)."""
 import numpy as np
 import pytest
 from scipy import stats
@@ -42,3 +42,16 @@ def test_forgy_draw_distinct_in_range():
     assert sorted(idx.tolist()) == list(range(50))
     idx = forgy_draw(99, 10**6, 100)
     assert idx.min() >= 0 and idx.max() < 10**6 and np.unique(idx).size == 100
+
+
+def test_published_known_answer_vectors():
+    """The generator is Philox-4x32-10 as published: the known-answer vectors of its authors'
+    Random123 distribution (tests/golden/philox4x32_10_kat.txt)."""
+    from conftest import read_golden
+    rows = read_golden("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for row in rows:
+        words = [int(x, 16) for x in row]
+        ctr, key, want = words[:4], words[4:6], words[6:10]
+        got = philox4x32_10(*ctr, *key)
+        assert [int(v) for v in got] == want
