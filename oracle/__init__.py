@@ -20,7 +20,15 @@ philox      Philox-4x32-10 counter-based generator and Box-Muller normals
 kmeans      Lloyd k-means, the paper's cost C_X (Eq. 1) and brute force
 spectral    exact spectral clustering by dense eigendecomposition (Section 2.1)
 dynamic     Algorithm 1 (dynamic CSC) driver with the feature splice (Eq. 6)
+compressive compressive k-means: variable-density sampling, reduced k-means,
+            Tikhonov interpolation by k low-pass filterings (Section 2.2, step 2)
+grad        gradients of a feature-space loss through the filter (coefficients
+            and edge weights; the paper has no derivative)
+similarity  edge similarity ||L_t - L_{t-1}||_F and Corollary 4.2's bound
+            (Definition 4.1, Section 4)
 
-Parity status of every function is stated in its module header.
+Parity status of every function is stated in its module header.  The
+eigencount also has the alternative trace estimator (chebyshev.trace_count).
 """
 from . import laplacian, chebyshev, philox, kmeans, spectral, dynamic  # noqa: F401
+from . import compressive, grad, similarity  # noqa: F401
