@@ -83,20 +83,22 @@ def quantise(s: np.ndarray):
     return q, big_e
 
 
-def draw_nodes(seed: int, n_draws: int, prefix: np.ndarray) -> np.ndarray:
-    """The n_draws drawn node indices (with repetitions), in draw order."""
-    prefix = np.asarray(prefix, dtype=np.int64)
-    total = int(prefix[-1])
+def draw_positions(seed: int, n_draws: int, total: int) -> list[int]:
+    """u_t = floor(U_t T / 2^64) in [0, T) for t < n_draws, U_t = x0 2^32 + x1 of Philox
+    counter (t, 0, 0, 2) under the seed."""
     k0 = seed & 0xFFFFFFFF
     k1 = (seed >> 32) & 0xFFFFFFFF
     t = np.arange(n_draws, dtype=np.uint64)
     x0, x1, _, _ = px.philox4x32_10(t, 0, 0, 2, k0, k1)
-    out = np.empty(n_draws, dtype=np.int64)
-    for i in range(n_draws):
-        big_u = (int(x0[i]) << 32) | int(x1[i])
-        u = (big_u * total) >> 64
-        out[i] = int(np.searchsorted(prefix, u, side="right"))
-    return out
+    return [(((int(x0[i]) << 32) | int(x1[i])) * total) >> 64 for i in range(n_draws)]
+
+
+def draw_nodes(seed: int, n_draws: int, prefix: np.ndarray) -> np.ndarray:
+    """The n_draws drawn node indices (with repetitions), in draw order: for each u_t the
+    smallest i with P_i > u_t."""
+    prefix = np.asarray(prefix, dtype=np.int64)
+    us = draw_positions(seed, n_draws, int(prefix[-1]))
+    return np.array([int(np.searchsorted(prefix, u, side="right")) for u in us], dtype=np.int64)
 
 
 def sample(theta: np.ndarray, n_draws: int, seed: int):

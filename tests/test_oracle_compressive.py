@@ -41,6 +41,31 @@ def test_draw_law_matches_the_weights():
     assert not np.array_equal(drawn[:100], ck.draw_nodes(12346, 100, prefix))
 
 
+def test_draws_follow_the_inverse_distribution_by_brute_force():
+    """Each drawn node is the smallest i whose prefix sum exceeds the draw position; nodes
+    with zero weight (equal consecutive prefix sums) are never hit, also at the boundaries."""
+    q = np.array([0, 3, 0, 0, 2, 5, 0, 1], dtype=np.int64)
+    prefix = np.cumsum(q)
+    total = int(prefix[-1])
+    us = ck.draw_positions(77, 3000, total)
+    nodes = ck.draw_nodes(77, 3000, prefix)
+    assert min(us) >= 0 and max(us) < total
+    for u, node in zip(us, nodes):
+        brute = next(i for i in range(q.size) if prefix[i] > u)
+        assert node == brute
+    assert set(np.unique(nodes)) == {1, 4, 5, 7}
+    # every position is reachable: position u maps to node brute(u) for all u < T
+    assert sorted(set(us)) == list(range(total))
+
+
+def test_uniform_energies_give_unit_weights():
+    """Rows of equal energy: uniform sampling, so every weight T / (n q_i) is exactly 1."""
+    theta = np.tile(np.array([[0.5, -1.0, 2.0]], dtype=np.float32), (37, 1))
+    omega, q, total = ck.sample(theta, 20, 3)
+    assert np.all(q == q[0]) and total == q.size * int(q[0])
+    np.testing.assert_array_equal(ck.sample_weights(q, total, omega), np.ones(omega.size))
+
+
 @pytest.mark.parametrize("scale", [1e-30, 1e-3, 1.0, 1e6, 1e30])
 def test_quantisation_is_exact_and_fine(scale):
     rng = np.random.default_rng(4)
