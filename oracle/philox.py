@@ -18,8 +18,11 @@ counter-based generator from its published definition:
   with U = x0 * 2^32 + x1; a repeated index is redrawn with attempt + 1.
 
 Pins (tests/test_oracle_philox.py): the published known-answer vectors of
-Philox-4x32-10 (tests/golden/philox4x32_10_kat.txt), and the statistics of the
-signals (mean, variance 1/d, normality, column independence).
+Philox-4x32-10 (tests/golden/philox4x32_10_kat.txt); the statistics of the
+signals (mean, variance 1/d, normality, column independence); the index map
+on the published output words, evaluated by hand (tests/golden/forgy_index_map.txt);
+chi-square uniformity of single Forgy draws over many seeds and of ordered
+distinct pairs (the redraw of a repeated index).
 """
 from __future__ import annotations
 
@@ -63,6 +66,13 @@ def gaussian_columns(seed: int, n: int, col_ids, d: int) -> np.ndarray:
     return z / np.sqrt(float(d))
 
 
+def index_from_words(x0: int, x1: int, n: int) -> int:
+    """Index in [0, n) of one draw: floor(U n / 2^64) with the 64-bit word U = x0 2^32 + x1
+    (exact integer arithmetic, so every index has probability within 2^-64 n of 1/n)."""
+    u = (int(x0) << 32) | int(x1)
+    return (u * int(n)) >> 64
+
+
 def forgy_draw(seed: int, n: int, k: int) -> np.ndarray:
     """k distinct row indices in [0, n) from the counter-based stream 1."""
     k0 = seed & 0xFFFFFFFF
@@ -73,8 +83,7 @@ def forgy_draw(seed: int, n: int, k: int) -> np.ndarray:
         attempt = 0
         while True:
             x0, x1, _, _ = philox4x32_10(j, attempt, 0, 1, k0, k1)
-            u = (int(x0) << 32) | int(x1)
-            idx = (u * n) >> 64
+            idx = index_from_words(x0, x1, n)
             if idx not in seen:
                 break
             attempt += 1

@@ -207,6 +207,27 @@ def test_trace_count_is_unbiased_for_trace_h():
     assert target > float(np.sum(cb.response(a, lam) ** 2))
 
 
+def test_count_tolerance_is_twice_the_ideal_projector_spread():
+    """tau = max(0.5, 2 sqrt(2k/c)) is twice the spread of the count under the ideal low pass.
+    With Psi = U_k U_k^T R (Eq. 3's projector on a graph's k lowest eigenvectors) and c signals
+    of variance 1/d, (d/c) ||Psi||_F^2 is chi-square with kc degrees of freedom over c: mean k and
+    standard deviation sqrt(2k/c).  Both are measured here over 3000 seeds with the oracle's
+    eigencount, and the oracle's tolerance must equal max(0.5, twice the measured spread)."""
+    g = W.sbm_graph(120, 4, 12, 10, seed=3)
+    lap = lp.normalized_laplacian_dense(g.n, g.row_ptr, g.col_idx)
+    hk = sp_.ideal_projector(lap, 10)
+    rng = np.random.default_rng(8)
+    for k, c, d in ((10, 8, 64), (4, 32, 48), (10, 128, 256)):
+        proj = hk if k == 10 else sp_.ideal_projector(lap, k)
+        counts = np.array([cb.eigencount(proj @ (rng.standard_normal((g.n, c)) / math.sqrt(d)), d)
+                           for _ in range(3000)])
+        sd = counts.std(ddof=1)
+        assert abs(counts.mean() - k) < 4.0 * math.sqrt(2.0 * k / c) / math.sqrt(counts.size)
+        assert abs(sd / math.sqrt(2.0 * k / c) - 1.0) < 0.06, (k, c, sd)
+        tau = cb.count_tolerance(k, c)
+        assert abs(tau - max(0.5, 2.0 * sd)) <= 0.06 * max(0.5, 2.0 * sd), (k, c, tau, sd)
+
+
 def test_count_monotone_in_cutoff():
     g, lt = _small_graph()
     r = W.gaussian_block(g.n, 8, 8, seed=4).astype(np.float64)

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 from scipy import stats
 
-from oracle.philox import forgy_draw, gaussian_columns, philox4x32_10
+from oracle.philox import forgy_draw, gaussian_columns, index_from_words, philox4x32_10
 
 
 def test_gaussian_moments_and_normality():
@@ -42,6 +42,43 @@ def test_forgy_draw_distinct_in_range():
     assert sorted(idx.tolist()) == list(range(50))
     idx = forgy_draw(99, 10**6, 100)
     assert idx.min() >= 0 and idx.max() < 10**6 and np.unique(idx).size == 100
+
+
+def test_forgy_index_map_on_published_words():
+    """floor(U n / 2^64) on the published output words, worked out by hand
+    (tests/golden/forgy_index_map.txt): power-of-two n reads off the top bits of x0, and at
+    n = 2^31 - 2 the low word x1 decides the result, so a map that drops x1, reduces U mod n or
+    uses one word only fails."""
+    from conftest import read_golden
+    rows = read_golden("forgy_index_map.txt")
+    assert len(rows) == 12
+    for x0, x1, n, want in rows:
+        assert index_from_words(int(x0, 16), int(x1, 16), int(n)) == int(want)
+    # the words come from the known-answer outputs of the generator itself
+    kat = read_golden("philox4x32_10_kat.txt")
+    words = {(int(r[6], 16), int(r[7], 16)) for r in kat}
+    assert {(int(x0, 16), int(x1, 16)) for x0, x1, _, _ in rows} == words
+
+
+def test_forgy_single_draw_uniform_over_seeds():
+    """The first Forgy index is uniform on [0, n): chi-square over 7000 seeds (n = 7)."""
+    n, seeds = 7, 7000
+    counts = np.bincount([int(forgy_draw(s, n, 1)[0]) for s in range(seeds)], minlength=n)
+    assert counts.size == n
+    assert stats.chisquare(counts).pvalue > 1e-3
+
+
+def test_forgy_ordered_pairs_uniform_over_seeds():
+    """With the redraw of a repeated index, (first, second) is uniform over the n (n - 1)
+    ordered distinct pairs: chi-square over 6000 seeds (n = 4, 12 pairs)."""
+    n, seeds = 4, 6000
+    counts = np.zeros((n, n), dtype=np.int64)
+    for s in range(seeds):
+        a, b = forgy_draw(1000 + s, n, 2)
+        counts[a, b] += 1
+    assert np.all(np.diag(counts) == 0)
+    off = counts[~np.eye(n, dtype=bool)]
+    assert stats.chisquare(off).pvalue > 1e-3
 
 
 def test_published_known_answer_vectors():
