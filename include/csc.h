@@ -272,9 +272,11 @@ csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_graph_desc* 
 
 /* ---------------------------------------------------------------- allocation-free variant */
 
-/* The paper has no counterpart to this entry point; it exists for callers that cannot
- * allocate device memory while they run (code inside a CUDA stream capture, programs whose
- * caching allocator owns all device memory, services that forbid allocation after start-up).
+/* The paper has no counterpart to this entry point.  It exists for callers that cannot call
+ * cudaMalloc while they run: a framework whose caching allocator reserved the device memory up
+ * front (a further allocation may fail, or fragment the memory that allocator manages), or a
+ * latency-bound service that forbids allocation after start-up (cudaMalloc and cudaFree can
+ * synchronise the whole device and stall every other stream).
  *
  * Computes the same Psi~ = h(L) R and trace moments as csc_cheb_filter, for a graph given
  * directly as caller-owned device CSR (row_ptr int64[n+1], col_idx int32[nnz], vals float[nnz]
@@ -282,16 +284,17 @@ csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_graph_desc* 
  * caller-owned device signal block R (float32, n x c, leading dimension ldr >= c) and a
  * caller-owned device output psi_out (float32, n x c, leading dimension ldp >= c; NULL:
  * moments only).  mu_out: host double[2m+1] or NULL.  Work runs on cuda_stream (NULL = default
- * stream); the call returns when the results are written.
+ * stream); the call copies each tile's moments to the host, synchronises that stream and
+ * returns when the results are written.
  *
  * It allocates nothing: all scratch lives in one fixed static device array of about 11 MB,
  * which every GPU that loads this library holds until the process exits.  Limits: n <= 65,536,
  * nnz <= 4,194,304, 1 <= m <= 128 (any c; columns are processed 8 at a time); larger sizes
  * return CSC_ELIMIT.  The first call on a device looks up that array's device address (which
  * loads the module), so make the first call before any stream capture.  Every call shares the
- * one array: calls that overlap on the GPU (other streams or host threads) race on it and must
- * be serialised by the caller.  Errors: CSC_EINVAL (bad pointers or sizes), CSC_ELIMIT,
- * CSC_ECUDA. */
+ * one array, which keeps the last call's contents: calls that overlap on the GPU (other streams
+ * or host threads) race on it and must be serialised by the caller.  Errors: CSC_EINVAL (bad
+ * sizes, a null R, or an array that is not device memory), CSC_ELIMIT, CSC_ECUDA. */
 csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr,
                                    const int32_t* col_idx, const float* vals, int m,
                                    double lambda_c, const float* R, int c, int64_t ldr,

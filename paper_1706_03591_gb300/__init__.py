@@ -435,16 +435,38 @@ def cheb_filter_layer(context, n: int, row_ptr, col_idx, weights, coef, R, strid
 def csc_cheb_filter_noalloc(n: int, row_ptr, col_idx, vals, m: int, lambda_c: float, R,
                             psi_out=None, want_moments: bool = True, stream=None):
     """Allocation-free filter of a device signal block R over a device CSR graph (small
-    graphs only; see include/csc.h).  Returns the 2m+1 trace moments (or None)."""
-    rp, w1, _, _ = _arr(row_ptr, "row_ptr")
-    ci, w2, _, _ = _arr(col_idx, "col_idx")
-    vv, _, _, _ = _arr(vals, "vals")
-    r, w3, _, ldr = _arr(R, "R")
-    pp, _, _, ldp = _arr(psi_out, "psi_out")
+    graphs only; see include/csc.h).  Every array must be a CUDA torch tensor: row_ptr int64
+    [n+1], col_idx int32 [nnz], vals float32 [nnz] or None, R float32 [n, c], psi_out float32
+    [n, c] or None.  Returns the 2m+1 trace moments (or None)."""
+    import torch
+    n = int(n)
+    named = (("row_ptr", row_ptr, torch.int64), ("col_idx", col_idx, torch.int32),
+             ("vals", vals, torch.float32), ("R", R, torch.float32), ("psi_out", psi_out, torch.float32))
+    for kind, x, dt in named:
+        if x is None and kind in ("vals", "psi_out"):
+            continue
+        if not (_is_torch(x) and x.is_cuda):
+            raise TypeError(f"csc_cheb_filter_noalloc: {kind} must be a CUDA tensor")
+        if x.dtype != dt:
+            raise TypeError(f"csc_cheb_filter_noalloc: {kind} must be {dt}, got {x.dtype}")
+    if row_ptr.dim() != 1 or row_ptr.numel() != n + 1:
+        raise ValueError("csc_cheb_filter_noalloc: row_ptr must hold n + 1 entries")
+    if col_idx.dim() != 1 or not col_idx.is_contiguous():
+        raise ValueError("csc_cheb_filter_noalloc: col_idx must be a contiguous vector")
+    nnz = int(col_idx.numel())
+    if vals is not None and (vals.dim() != 1 or vals.numel() != nnz or not vals.is_contiguous()):
+        raise ValueError("csc_cheb_filter_noalloc: vals must hold one weight per stored edge")
+    if R.dim() != 2 or R.shape[0] != n:
+        raise ValueError("csc_cheb_filter_noalloc: R must be n x c")
     c = int(R.shape[1])
-    nnz = int(col_idx.numel() if _is_torch(col_idx) else np.asarray(col_idx).size)
+    if psi_out is not None and (psi_out.dim() != 2 or tuple(psi_out.shape) != (n, c)):
+        raise ValueError("csc_cheb_filter_noalloc: psi_out must be n x c")
+    rp, _, _, _ = _arr(row_ptr, "row_ptr")
+    ci, _, _, _ = _arr(col_idx, "col_idx")
+    vv, _, _, _ = _arr(vals, "vals")
+    r, _, _, ldr = _arr(R, "R")
+    pp, _, _, ldp = _arr(psi_out, "psi_out")
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
     mu = np.zeros(2 * m + 1) if want_moments else None
     _check(_lib().csc_cheb_filter_noalloc(

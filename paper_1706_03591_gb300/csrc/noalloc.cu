@@ -1,17 +1,22 @@
 // Allocation-free Chebyshev filtering for small graphs (csc_cheb_filter_noalloc).
 //
-// Some callers cannot allocate device memory while they run: code that executes inside a
-// stream capture, or under a caching allocator that owns every allocation, or in a service
-// that forbids allocations after start-up.  This entry point takes only caller-owned buffers
-// (graph, signals, output) and keeps all of its scratch in one file-scope static device array
-// of fixed size, sized for graphs of at most kMaxN nodes and kMaxNnz stored edges and orders
-// of at most kMaxM.  The array exists on every GPU that loads this library, until exit.
+// Some callers cannot call cudaMalloc while they run.  A framework whose caching allocator
+// reserved the device memory up front may have nothing left to give, and an allocation outside
+// that allocator fragments what it manages.  A latency-bound service may forbid allocation
+// after start-up, because cudaMalloc and cudaFree can synchronise the whole device and stall
+// every other stream.  This entry point takes only caller-owned device buffers (graph,
+// signals, output) and keeps all of its scratch in one file-scope static device array of fixed
+// size, sized for graphs of at most kMaxN nodes and kMaxNnz stored edges and orders of at most
+// kMaxM.  The array exists on every GPU that loads this library, until the process exits.
 //
-// It runs the same kernels as csc_cheb_filter with a column tile of 8; the scratch address
-// is looked up once per device with cudaGetSymbolAddress (the first call on a device does
-// that look-up, which loads the module, so it should come before any stream capture).  All
-// calls share the one array: calls that overlap on the GPU (different streams, or different
-// host threads) race on it and must be serialised by the caller.
+// It runs the same kernels as csc_cheb_filter with a column tile of 8.  The host reads the
+// moments of each tile back through host memory and synchronises the caller's stream before
+// returning.  The scratch address is looked up once per device with cudaGetSymbolAddress: the
+// first call on a device does that look-up, which loads the module, so that first call should
+// come before any stream capture.  All calls share the one array, which keeps the last call's
+// contents (every region a call reads is written by that call first): calls that overlap on
+// the GPU (different streams, or different host threads) race on it and must be serialised by
+// the caller.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -65,20 +70,6 @@ cudaError_t scratch_address(unsigned char** out) {
   return cudaSuccess;
 }
 
-// Same coefficients as the context path (Section 3.3 reading).
-void coeffs(int m, double lambda_c, double* a) {
-  const double x_c = std::min(1.0, std::max(-1.0, lambda_c - 1.0));
-  const double theta = std::acos(x_c);
-  const double mp2 = m + 2.0;
-  const double alpha = M_PI / mp2;
-  for (int j = 0; j <= m; ++j) {
-    const double c = j == 0 ? (M_PI - theta) / M_PI : -2.0 * std::sin(j * theta) / (j * M_PI);
-    const double g = ((mp2 - j) * std::sin(alpha) * std::cos(j * alpha) +
-                      std::cos(alpha) * std::sin(j * alpha)) / (mp2 * std::sin(alpha));
-    a[j] = g * c;
-  }
-}
-
 }  // namespace
 
 #define NA_CHECK(call)                           \
@@ -95,6 +86,17 @@ extern "C" csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int6
       !(lambda_c >= 0.0 && lambda_c <= 2.0) || (psi_out && ldp < c))
     return CSC_EINVAL;
   if (n > kMaxN || nnz > kMaxNnz || m > kMaxM) return CSC_ELIMIT;
+  // every array is read or written by kernels: host pointers are refused
+  const void* dev_ptrs[] = {row_ptr, nnz > 0 ? col_idx : nullptr, vals, R, psi_out};
+  for (const void* p : dev_ptrs) {
+    if (p == nullptr) continue;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return CSC_EINVAL;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return CSC_EINVAL;
+  }
   unsigned char* base = nullptr;
   NA_CHECK(scratch_address(&base));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -123,7 +125,7 @@ extern "C" csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int6
   double* ef = reinterpret_cast<double*>(base + kOffEf);
   double a[kMaxM + 1];
   float af[kMaxM + 1];
-  coeffs(m, lambda_c, a);
+  csc::filter_coeffs(m, lambda_c, a);
   for (int j = 0; j <= m; ++j) af[j] = (float)a[j];
   NA_CHECK(cudaMemcpyAsync(coef, af, (size_t)(m + 1) * 4, cudaMemcpyHostToDevice, s));
   const int grid = std::min(csc::cheb_grid(kTile), kMaxGrid);
