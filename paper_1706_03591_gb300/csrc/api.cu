@@ -54,13 +54,10 @@ int grid_for(const void* kernel, int block, size_t smem) {
   return std::max(1, per_sm) * num_sms();
 }
 
-}  // namespace csc
-
-namespace {
-
-// ------------------------------------------------------------------ host math (Section 3.3)
-
-void coeffs(int m, double lambda_c, double* a) {
+// Jackson-damped Chebyshev coefficients of the step 1[lambda <= lambda_c] (Section 3.3
+// reading): a_j = g_j c_j with x = lambda - 1, theta = arccos(lambda_c - 1),
+// c_0 = (pi - theta)/pi, c_j = -2 sin(j theta)/(j pi) and the Jackson factors g_j of order m.
+void filter_coeffs(int m, double lambda_c, double* a) {
   const double x_c = std::min(1.0, std::max(-1.0, lambda_c - 1.0));
   const double theta = std::acos(x_c);
   const double mp2 = m + 2.0;
@@ -72,6 +69,14 @@ void coeffs(int m, double lambda_c, double* a) {
     a[j] = g * c;
   }
 }
+
+}  // namespace csc
+
+namespace {
+
+using csc::filter_coeffs;
+
+// ------------------------------------------------------------------ host math (Section 3.3)
 
 double count_moments(int m, const double* mu, const double* a, int d, int c) {
   double s = 0.0;
@@ -224,7 +229,7 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
   ALLOC_OK(csc::ensure(ctx->ef, (size_t)rows * 8));
   ALLOC_OK(csc::ensure(ctx->coef, (size_t)(m + 1) * 4));
   std::vector<double> a(m + 1);
-  coeffs(m, lambda_c, a.data());
+  filter_coeffs(m, lambda_c, a.data());
   std::vector<float> af(a.begin(), a.end());
   CUDA_OK(cudaMemcpyAsync(ctx->coef.ptr, af.data(), af.size() * 4, cudaMemcpyHostToDevice, s));
   const int t0_dtype = src.philox ? ctx->opts.precision : src.dtype;
@@ -310,7 +315,7 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
 
 double count_at(const csc_ctx* ctx, double lam, int d, int c) {
   std::vector<double> a(ctx->last_m + 1);
-  coeffs(ctx->last_m, lam, a.data());
+  filter_coeffs(ctx->last_m, lam, a.data());
   if (ctx->opts.estimator == 1) return count_moments_trace(ctx->last_m, ctx->mu.data(), a.data(), d, c);
   return count_moments(ctx->last_m, ctx->mu.data(), a.data(), d, c);
 }
@@ -536,7 +541,7 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
 
 csc_status csc_filter_coeffs(int m, double lambda_c, double* a_out) {
   if (m < 0 || !a_out || !(lambda_c == lambda_c)) return CSC_EINVAL;
-  coeffs(m, lambda_c, a_out);
+  filter_coeffs(m, lambda_c, a_out);
   return CSC_OK;
 }
 
@@ -546,7 +551,7 @@ csc_status csc_count_from_moments(int m, const double* mu, double lambda_c, int 
                                   double* count_out) {
   if (m < 0 || !mu || d < 1 || c < 1 || !count_out) return CSC_EINVAL;
   std::vector<double> a(m + 1);
-  coeffs(m, lambda_c, a.data());
+  filter_coeffs(m, lambda_c, a.data());
   *count_out = count_moments(m, mu, a.data(), d, c);
   return CSC_OK;
 }
@@ -555,7 +560,7 @@ csc_status csc_trace_count_from_moments(int m, const double* mu, double lambda_c
                                        double* count_out) {
   if (m < 0 || !mu || d < 1 || c < 1 || !count_out) return CSC_EINVAL;
   std::vector<double> a(m + 1);
-  coeffs(m, lambda_c, a.data());
+  filter_coeffs(m, lambda_c, a.data());
   *count_out = count_moments_trace(m, mu, a.data(), d, c);
   return CSC_OK;
 }
@@ -568,7 +573,7 @@ csc_status csc_lambda_search_moments(int m, const double* mu, int d, int c, int 
     return CSC_EINVAL;
   std::vector<double> a(m + 1);
   auto count = [&](double lam) {
-    coeffs(m, lam, a.data());
+    filter_coeffs(m, lam, a.data());
     return count_moments(m, mu, a.data(), d, c);
   };
   search(count, k, tau, lambda_prev, max_steps, lambda_out, count_out, evals_out);

@@ -42,19 +42,6 @@ int next_pow2(int v) {
   return p;
 }
 
-void coeffs(int m, double lambda_c, double* a) {
-  const double x_c = std::min(1.0, std::max(-1.0, lambda_c - 1.0));
-  const double theta = std::acos(x_c);
-  const double mp2 = m + 2.0;
-  const double alpha = M_PI / mp2;
-  for (int j = 0; j <= m; ++j) {
-    const double c = j == 0 ? (M_PI - theta) / M_PI : -2.0 * std::sin(j * theta) / (j * M_PI);
-    const double g = ((mp2 - j) * std::sin(alpha) * std::cos(j * alpha) +
-                      std::cos(alpha) * std::sin(j * alpha)) / (mp2 * std::sin(alpha));
-    a[j] = g * c;
-  }
-}
-
 // Size class of a graph for the autotuner: log2 of the stored edges and the column bucket.
 uint64_t size_class(const csc_graph_desc& g) {
   const int lg = (int)std::ceil(std::log2((double)std::max<int64_t>(g.nnz, 2)));
@@ -218,7 +205,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   for (int g = 0; g < n_graphs; ++g) {
     const csc_graph_desc& d = descs[g];
     const GraphPlan& p = plan[g];
-    coeffs(m, d.lambda_c, a.data());
+    csc::filter_coeffs(m, d.lambda_c, a.data());
     for (int j = 0; j <= m; ++j) coef_h[(size_t)g * (m + 1) + j] = (float)a[j];
     for (int t = 0; t < p.ntiles; ++t) {
       csc::BatchTile bt{};

@@ -58,6 +58,10 @@ int edge_blocks(int64_t nnz);
 int num_sms();
 int grid_for(const void* kernel, int block, size_t smem = 0);
 
+// a[0..m]: Jackson-damped Chebyshev coefficients of the low-pass of cutoff lambda_c
+// (Section 3.3), shared by every entry point that filters.
+void filter_coeffs(int m, double lambda_c, double* a);
+
 // ------------------------------------------------------------------ graph kernels (graph.cu)
 
 cudaError_t launch_graph_prep(const Graph& g, cudaStream_t s);

@@ -27,6 +27,28 @@ def read_golden(name):
     return rows
 
 
+def rel(a, b):
+    """Relative Frobenius error ||a - b|| / ||b|| in float64."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def fp32_floor(lt, r, a, ref):
+    """Error against ``ref`` of a plain float32 evaluation of sum_j a_j T_j(L~) R by the
+    three-term recursion: the rounding floor that any float32 implementation of the filter
+    meets at this size (large when the output cancels, e.g. h(1) on an edgeless graph)."""
+    lt32 = lt.astype(np.float32)
+    a32 = np.asarray(a, dtype=np.float32)
+    t_prev = np.asarray(r, dtype=np.float32)
+    t_cur = lt32 @ t_prev
+    out = a32[0] * t_prev + a32[1] * t_cur
+    for j in range(2, a32.size):
+        t_prev, t_cur = t_cur, 2.0 * (lt32 @ t_cur) - t_prev
+        out += a32[j] * t_cur
+    return rel(out, ref)
+
+
 def graph_from_edges(n, edges):
     """CSR (row_ptr int64, col_idx int32) of an undirected edge list."""
     adj = [[] for _ in range(n)]

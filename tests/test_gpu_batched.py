@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from conftest import fp32_floor
 from oracle import chebyshev as cb
 from oracle import laplacian as lp
 from oracle.philox import gaussian_columns
@@ -18,21 +19,6 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def fp32_floor(lt, r, m, lam, ref):
-    """Error of a plain float32 evaluation of the same recursion against float64 (the rounding
-    floor any float32 implementation meets; large when the filter output cancels, e.g. h(1)
-    for an edgeless graph with a cutoff below 1)."""
-    lt32 = lt.astype(np.float32)
-    a32 = cb.filter_coefficients(m, lam).astype(np.float32)
-    t_prev = r.astype(np.float32)
-    t_cur = lt32 @ t_prev
-    out = a32[0] * t_prev + a32[1] * t_cur
-    for j in range(2, m + 1):
-        t_prev, t_cur = t_cur, 2.0 * (lt32 @ t_cur) - t_prev
-        out += a32[j] * t_cur
-    return rel(out, ref)
 
 
 def _batch(seed=0, count=7):
@@ -146,7 +132,7 @@ def test_batched_weighted_edgeless_tiny_and_several_waves(gpu_lib):
         r = gaussian_columns(77 + i, g.n, cols, c)
         ref = cb.cheb_filter(lt, r, m, lam)
         got = dsc["psi"].cpu().numpy()[:, cols]
-        tol = max(FP32_TOL, 2.0 * fp32_floor(lt, r, m, lam, ref))
+        tol = max(FP32_TOL, 2.0 * fp32_floor(lt, r, cb.filter_coefficients(m, lam), ref))
         assert rel(got, ref) < tol, (i, rel(got, ref), tol)
         if g.n < 1000:
             mu_ref = cb.moments(lt, r, 2 * m)

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from conftest import fp32_floor
 from oracle import chebyshev as cb
 from oracle import grad as gr
 from oracle import laplacian as lp
@@ -24,20 +25,6 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def fp32_floor(lt, r, a, ref):
-    """Error of a plain float32 evaluation of the same recursion against float64 (the rounding
-    floor any float32 implementation meets at this size)."""
-    lt32 = lt.astype(np.float32)
-    a32 = np.asarray(a, dtype=np.float32)
-    t_prev = r.astype(np.float32)
-    t_cur = lt32 @ t_prev
-    out = a32[0] * t_prev + a32[1] * t_cur
-    for j in range(2, a.size):
-        t_prev, t_cur = t_cur, 2.0 * (lt32 @ t_cur) - t_prev
-        out += a32[j] * t_cur
-    return rel(out, ref)
 
 
 def sym_weights(g, seed):

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from conftest import fp32_floor
 from oracle import chebyshev as cb
 from oracle import kmeans as km
 from oracle import laplacian as lp
@@ -385,20 +386,6 @@ def test_algorithm1_dynamic_bf16_storage(gpu_lib, cfg1_graph):
             prev = lab
 
 
-def fp32_floor(lt, r, m, lam, ref):
-    """Error of a plain float32 evaluation of the same recursion against float64: the
-    rounding floor any float32 implementation of the filter meets at this size."""
-    lt32 = lt.astype(np.float32)
-    a32 = cb.filter_coefficients(m, lam).astype(np.float32)
-    t_prev = r.astype(np.float32)
-    t_cur = lt32 @ t_prev
-    out = a32[0] * t_prev + a32[1] * t_cur
-    for j in range(2, m + 1):
-        t_prev, t_cur = t_cur, 2.0 * (lt32 @ t_cur) - t_prev
-        out += a32[j] * t_cur
-    return rel(out, ref)
-
-
 def test_full_size_sampled_columns(gpu_lib):
     """n = 1e6 Zipf SBM (degree 30), 64 columns, m = 100 in the bench's tile configuration;
     the oracle recomputes two sampled columns in float64 (columns are independent).
@@ -418,7 +405,7 @@ def test_full_size_sampled_columns(gpu_lib):
     lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
     cols = [0, 37]
     ref = cb.cheb_filter(lt, r[:, cols].astype(np.float64), m, lam)
-    floor = fp32_floor(lt, r[:, cols], m, lam, ref)
+    floor = fp32_floor(lt, r[:, cols], cb.filter_coefficients(m, lam), ref)
     err = rel(got[:, cols], ref)
     print(f"full-size sampled columns: GPU error {err:.3e}, float32 floor {floor:.3e}")
     assert err < max(FP32_TOL, 2.0 * floor)
