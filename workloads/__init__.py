@@ -33,6 +33,12 @@ __all__ = [
     "clustered_points",
     "forgy_indices",
     "random_csr",
+    "node_reassign",
+    "sbm_perturb",
+    "TorchGraph",
+    "chung_lu_graph_torch",
+    "edge_redraw_torch",
+    "sbm_graph_torch",
 ]
 
 
@@ -188,7 +194,7 @@ def sbm_graph(n: int, sizes, avg_degree: float, ratio: float, seed: int) -> Grap
     u, v = _sbm_draw_edges(rng, counts, a_idx, b_idx, offsets, sizes, perm)
     upper = _canonical_upper(n, u, v)
     model = dict(kind="sbm", sizes=sizes, offsets=offsets, members=perm,
-                 a_idx=a_idx, b_idx=b_idx, weight=pairs * prob)
+                 a_idx=a_idx, b_idx=b_idx, weight=pairs * prob, p_in=p_in, p_out=p_out)
     return Graph(n=n, keys=_symmetric_keys(n, upper), labels=labels, model=model)
 
 
@@ -284,6 +290,67 @@ def edge_redraw(g: Graph, frac: float, seed: int) -> Graph:
     return Graph(n=n, keys=_symmetric_keys(n, new_upper), labels=g.labels, model=g.model)
 
 
+def node_reassign(g: Graph, frac: float, seed: int) -> Graph:
+    """Node reassignment churn of an SBM (Section 5.1): pick round(frac n) nodes uniformly, remove
+    every edge with an end among them, move each to one of the other k - 1 blocks uniformly at
+    random, and reconnect them by the model's probabilities (p_in inside the new block, p_out
+    across): edges to the unpicked nodes are drawn per (picked node, block) as binomial counts
+    with uniform endpoints, edges among the picked nodes as an SBM on the picked set.  The
+    returned graph carries the new labels and the model of the new block sizes, so later churn
+    draws from the perturbed model."""
+    md = g.model
+    if md.get("kind") != "sbm":
+        raise ValueError("node_reassign: graph model must be sbm")
+    rng = np.random.default_rng(seed)
+    n = g.n
+    k = int(md["sizes"].size)
+    p_in, p_out = md["p_in"], md["p_out"]
+    r = int(round(frac * n))
+    picked = np.sort(rng.choice(n, size=r, replace=False)).astype(np.int64)
+    is_picked = np.zeros(n, dtype=bool)
+    is_picked[picked] = True
+    labels = g.labels.astype(np.int64).copy()
+    labels[picked] = (labels[picked] + rng.integers(1, k, size=r)) % k
+    upper = g.upper_keys()
+    kept = upper[~(is_picked[upper // n] | is_picked[upper % n])]
+    # picked -> unpicked: per (picked node, block) binomial counts, uniform endpoints
+    rest = np.flatnonzero(~is_picked)
+    rest = rest[np.argsort(labels[rest], kind="stable")]
+    rest_sizes = np.bincount(labels[rest], minlength=k)
+    rest_off = np.concatenate([[0], np.cumsum(rest_sizes)[:-1]])
+    prob = np.where(labels[picked][:, None] == np.arange(k)[None, :], p_in, p_out)
+    cnt = rng.binomial(np.broadcast_to(rest_sizes, (r, k)), prob)
+    src = np.repeat(np.repeat(picked, k), cnt.ravel())
+    blk = np.repeat(np.tile(np.arange(k), r), cnt.ravel())
+    dst = rest[rest_off[blk] + np.floor(rng.random(blk.size) * rest_sizes[blk]).astype(np.int64)]
+    # picked <-> picked: the SBM restricted to the picked set
+    pk = picked[np.argsort(labels[picked], kind="stable")]
+    pk_sizes = np.bincount(labels[picked], minlength=k)
+    pk_off = np.concatenate([[0], np.cumsum(pk_sizes)[:-1]])
+    a_idx, b_idx, pairs, pprob = _sbm_pair_table(pk_sizes, p_in, p_out)
+    pcnt = rng.binomial(pairs.astype(np.int64), pprob)
+    pu, pv = _sbm_draw_edges(rng, pcnt, a_idx, b_idx, pk_off, np.maximum(pk_sizes, 1), pk)
+    new = _canonical_upper(n, np.concatenate([src, pu]), np.concatenate([dst, pv]))
+    sizes = np.bincount(labels, minlength=k).astype(np.int64)
+    members = np.argsort(labels, kind="stable").astype(np.int64)
+    offsets = np.zeros(k, dtype=np.int64)
+    np.cumsum(sizes[:-1], out=offsets[1:])
+    a_all, b_all, pairs_all, prob_all = _sbm_pair_table(sizes, p_in, p_out)
+    model = dict(kind="sbm", sizes=sizes, offsets=offsets, members=members, a_idx=a_all,
+                 b_idx=b_all, weight=pairs_all * prob_all, p_in=p_in, p_out=p_out)
+    out = Graph(n=n, keys=_symmetric_keys(n, _sorted_unique(np.concatenate([kept, new]))),
+                labels=labels.astype(np.int32), model=model)
+    out.model["reassigned"] = picked
+    return out
+
+
+def sbm_perturb(g: Graph, node_frac: float, edge_frac: float, seed: int) -> Graph:
+    """The combined perturbation of Section 5.2: node reassignment of node_frac of the nodes,
+    then edge redrawing of edge_frac of the edges."""
+    h = node_reassign(g, node_frac, seed)
+    return edge_redraw(h, edge_frac, seed + 1)
+
+
 def random_csr(n: int, avg_degree: float, seed: int, isolated: int = 0) -> Graph:
     """Erdos-Renyi-like graph (uniform endpoints), optionally with `isolated`
     nodes that receive no edges (for edge-case tests)."""
@@ -321,3 +388,205 @@ def forgy_indices(n: int, k: int, seed: int) -> np.ndarray:
     """k distinct row indices drawn uniformly (Forgy initialisation input)."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n, size=k, replace=False)).astype(np.int64)
+
+
+# ------------------------------------------------------------------ large graphs on a torch device
+#
+# The power-law workload has n = 8e6 nodes and about 2e8 stored edges; the numpy generators
+# above would spend minutes sorting 2e8 keys per snapshot.  The functions below draw the same
+# models (Chung-Lu with planted communities, edge redrawing) with torch on any device (the GPU
+# for full sizes, the CPU in tests), seeded by a torch.Generator, so the graph of a seed is
+# fixed for a device type and torch's generator.  They hold no arithmetic of the method.
+
+@dataclass
+class TorchGraph:
+    """Simple undirected graph on a torch device: sorted symmetric keys u*n+v (int64, both
+    directions, no self-loops or duplicates), the matching CSR (row_ptr int64[n+1], col_idx
+    int32[nnz]), planted labels and the model that edge redrawing samples from."""
+
+    n: int
+    keys: object
+    row_ptr: object
+    col_idx: object
+    labels: object
+    model: dict
+
+    @property
+    def nnz(self) -> int:
+        return int(self.keys.numel())
+
+    def to_numpy(self) -> Graph:
+        """The same graph as a numpy Graph (for the oracle and small checks)."""
+        g = Graph(n=self.n, keys=self.keys.cpu().numpy(),
+                  labels=self.labels.cpu().numpy() if self.labels is not None else None)
+        g._csr = (self.row_ptr.cpu().numpy(), self.col_idx.cpu().numpy())
+        return g
+
+
+def _t_upper_from_endpoints(torch, n, u, v):
+    keep = u != v
+    u, v = u[keep], v[keep]
+    lo = torch.minimum(u, v)
+    hi = torch.maximum(u, v)
+    return torch.unique(lo * n + hi, sorted=True)
+
+
+def _t_graph_from_upper(torch, n, upper, labels, model):
+    u = upper // n
+    v = upper - u * n
+    keys = torch.cat([upper, v * n + u]).sort().values
+    rows = keys // n
+    col_idx = (keys - rows * n).to(torch.int32)
+    counts = torch.bincount(rows, minlength=n)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=keys.device)
+    torch.cumsum(counts, 0, out=row_ptr[1:])
+    return TorchGraph(n=n, keys=keys, row_ptr=row_ptr, col_idx=col_idx, labels=labels, model=model)
+
+
+def _t_chung_lu_draw(torch, gen, model, count):
+    order, cw, labels = model["order"], model["cw"], model["labels"]
+    total = model["total"]
+    dev = cw.device
+    top = cw.numel() - 1
+
+    def pick(x):
+        return order[torch.clamp(torch.searchsorted(cw, x, right=True), max=top)]
+
+    u = pick(torch.rand(count, generator=gen, device=dev, dtype=torch.float64) * total)
+    intra = torch.rand(count, generator=gen, device=dev, dtype=torch.float64) >= model["mixing"]
+    r = torch.rand(count, generator=gen, device=dev, dtype=torch.float64)
+    cu = labels[u].long()
+    lo = torch.where(intra, model["lo_w"][cu], torch.zeros_like(r))
+    hi = torch.where(intra, model["hi_w"][cu], torch.full_like(r, total))
+    v = pick(lo + r * (hi - lo))
+    return u, v
+
+
+def _t_sbm_draw(torch, gen, model, count):
+    """count endpoint pairs from the SBM: block pair ~ its expected edge share, endpoints
+    uniform within the two blocks."""
+    share = model["weight"]
+    pair = torch.multinomial(share, count, replacement=True, generator=gen)
+    a, b = model["a_idx"][pair], model["b_idx"][pair]
+    sz, off, members = model["sizes_t"], model["offsets"], model["members"]
+    dev = share.device
+    ua = off[a] + torch.floor(torch.rand(count, generator=gen, device=dev, dtype=torch.float64)
+                              * sz[a]).to(torch.int64)
+    vb = off[b] + torch.floor(torch.rand(count, generator=gen, device=dev, dtype=torch.float64)
+                              * sz[b]).to(torch.int64)
+    return members[ua], members[vb]
+
+
+def chung_lu_graph_torch(n: int, exponent: float, avg_degree: float, k: int, mixing: float,
+                         seed: int, device="cpu") -> TorchGraph:
+    """The Chung-Lu model of ``chung_lu_graph`` drawn with torch on ``device``.
+
+    Expected degrees w_i ~ i^(-1/(exponent-1)), rescaled to mean avg_degree and capped at
+    sqrt(sum w); nodes randomly permuted; k planted communities (uniform labels).  Each of
+    round(sum(w)/2) edges picks u ~ w, then v ~ w within u's community with probability
+    1 - mixing, else v ~ w over all nodes.  Self-loops and duplicates are dropped; isolated
+    nodes are kept."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev).manual_seed(int(seed))
+    w = torch.arange(1, n + 1, dtype=torch.float64, device=dev) ** (-1.0 / (exponent - 1.0))
+    w *= avg_degree / w.mean()
+    w = torch.minimum(w, torch.sqrt(w.sum()))
+    w *= avg_degree / w.mean()
+    perm = torch.randperm(n, generator=gen, device=dev)
+    weight = torch.empty(n, dtype=torch.float64, device=dev)
+    weight[perm] = w
+    labels = torch.randint(0, k, (n,), generator=gen, device=dev, dtype=torch.int64).to(torch.int32)
+    order = torch.sort(labels.long(), stable=True).indices
+    cw = torch.cumsum(weight[order], 0)
+    counts = torch.bincount(labels.long(), minlength=k)
+    ends = torch.cumsum(counts, 0)
+    starts = ends - counts
+    zero = torch.zeros(k, dtype=torch.float64, device=dev)
+    lo_w = torch.where(starts > 0, cw[torch.clamp(starts - 1, min=0)], zero)
+    hi_w = torch.where(counts > 0, cw[torch.clamp(ends - 1, min=0)], lo_w)
+    model = dict(kind="chung_lu", order=order, cw=cw, labels=labels, lo_w=lo_w, hi_w=hi_w,
+                 mixing=float(mixing), total=float(cw[-1]))
+    m_edges = int(round(float(weight.sum()) / 2.0))
+    u, v = _t_chung_lu_draw(torch, gen, model, m_edges)
+    upper = _t_upper_from_endpoints(torch, n, u, v)
+    del u, v
+    return _t_graph_from_upper(torch, n, upper, labels, model)
+
+
+def edge_redraw_torch(g: TorchGraph, frac: float, seed: int) -> TorchGraph:
+    """Edge redrawing (Section 5.1) of a TorchGraph: remove round(frac |E|) uniformly random
+    edges, then add as many new edges (absent from the graph, no self-loops) drawn from the
+    graph's own model."""
+    import torch
+    n = g.n
+    dev = g.keys.device
+    gen = torch.Generator(device=dev).manual_seed(int(seed))
+    rows = g.keys // n
+    upper = g.keys[rows < g.keys - rows * n]
+    del rows
+    n_change = int(round(frac * upper.numel()))
+    if n_change == 0:
+        return g
+    drop = torch.randperm(upper.numel(), generator=gen, device=dev)[:n_change]
+    keep = torch.ones(upper.numel(), dtype=torch.bool, device=dev)
+    keep[drop] = False
+    kept = upper[keep]
+    added = torch.empty(0, dtype=torch.int64, device=dev)
+    while added.numel() < n_change:
+        want = (n_change - added.numel()) * 2 + 16
+        if g.model.get("kind") == "chung_lu":
+            u, v = _t_chung_lu_draw(torch, gen, g.model, want)
+        elif g.model.get("kind") == "sbm":
+            u, v = _t_sbm_draw(torch, gen, g.model, want)
+        else:
+            raise ValueError("edge_redraw_torch: graph model must be chung_lu or sbm")
+        cand = _t_upper_from_endpoints(torch, n, u, v)
+        pos = torch.clamp(torch.searchsorted(upper, cand), max=upper.numel() - 1)
+        present = upper[pos] == cand
+        if added.numel() > 0:
+            sa = added.sort().values
+            pa = torch.clamp(torch.searchsorted(sa, cand), max=sa.numel() - 1)
+            present |= sa[pa] == cand
+        cand = cand[~present]
+        cand = cand[torch.randperm(cand.numel(), generator=gen, device=dev)]
+        added = torch.cat([added, cand[: n_change - added.numel()]])
+    new_upper = torch.cat([kept, added]).sort().values
+    return _t_graph_from_upper(torch, n, new_upper, g.labels, g.model)
+
+
+def sbm_graph_torch(n: int, sizes, avg_degree: float, ratio: float, seed: int,
+                    device="cpu") -> TorchGraph:
+    """The stochastic block model of ``sbm_graph`` drawn with torch on ``device``: edges per
+    block pair ~ Binomial(#pairs, p) with p_in = ratio p_out solved for the node-average degree,
+    endpoints uniform within the blocks, duplicates merged, node ids randomly permuted."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev).manual_seed(int(seed))
+    if np.isscalar(sizes):
+        k = int(sizes)
+        sizes = np.full(k, n // k, dtype=np.int64)
+        sizes[: n - int(sizes.sum())] += 1
+    sizes = np.asarray(sizes, dtype=np.int64)
+    assert int(sizes.sum()) == n
+    p_in, p_out = _sbm_probs(sizes, avg_degree, ratio)
+    a_idx, b_idx, pairs, prob = _sbm_pair_table(sizes, p_in, p_out)
+    perm = torch.randperm(n, generator=gen, device=dev)
+    sz = torch.as_tensor(sizes, device=dev)
+    offsets = torch.cumsum(sz, 0) - sz
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    labels[perm] = torch.repeat_interleave(torch.arange(sizes.size, dtype=torch.int32, device=dev), sz)
+    counts = torch.binomial(torch.as_tensor(pairs, dtype=torch.float64, device=dev),
+                            torch.as_tensor(prob, dtype=torch.float64, device=dev), generator=gen)
+    counts = counts.to(torch.int64)
+    a = torch.repeat_interleave(torch.as_tensor(a_idx, device=dev), counts)
+    b = torch.repeat_interleave(torch.as_tensor(b_idx, device=dev), counts)
+    ua = offsets[a] + torch.floor(torch.rand(a.numel(), generator=gen, device=dev, dtype=torch.float64)
+                                  * sz[a]).to(torch.int64)
+    vb = offsets[b] + torch.floor(torch.rand(b.numel(), generator=gen, device=dev, dtype=torch.float64)
+                                  * sz[b]).to(torch.int64)
+    upper = _t_upper_from_endpoints(torch, n, perm[ua], perm[vb])
+    model = dict(kind="sbm", sizes=sizes, sizes_t=sz, offsets=offsets, members=perm,
+                 a_idx=torch.as_tensor(a_idx, device=dev), b_idx=torch.as_tensor(b_idx, device=dev),
+                 weight=torch.as_tensor(pairs * prob, dtype=torch.float64, device=dev))
+    return _t_graph_from_upper(torch, n, upper, labels, model)
