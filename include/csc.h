@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 3
+#define CSC_ABI_VERSION 4
 
 typedef struct csc_ctx csc_ctx;
 
@@ -219,6 +219,17 @@ csc_status csc_estimate_lambda_k(csc_ctx* ctx, int k, int m, int d, uint64_t see
  * dichotomy evaluations (0 when lambda_c was given or k <= 0), columns filtered. */
 csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k, double lambda_c,
                       double* lambda_out, double* count_out, int* evals_out, int* cols_out);
+
+/* The splice of Eq. 6 with new columns that the caller filtered (for example one shard of the
+ * columns per GPU, gathered afterwards): psi_new (float32, n x c, leading dimension ldp >= c,
+ * host or device per where) holds the filtered columns of the next c global column ids, in
+ * order; they overwrite the ring slots csc_filter would choose (c = d at the first snapshot or
+ * when p == 0, else c = d - floor(p d)), the row-normalised Theta_t is prepared for
+ * csc_cluster, and lambda_c (in [0, 2]) becomes the context's cutoff.  The global column
+ * counter advances by c, as in csc_filter.  n and d must stay the same across snapshots.
+ * Errors: CSC_EINVAL (bad arguments or a c that does not match), CSC_ENOMEM, CSC_ECUDA. */
+csc_status csc_splice(csc_ctx* ctx, int64_t n, int d, double p, const float* psi_new, int c, int64_t ldp,
+                      int where, double lambda_c);
 
 /* Copies Theta_t (normalized = 0, float32 ring in slot order) or the row-normalised
  * features y_i = theta_i / ||theta_i|| (normalized = 1) into dst (n x d, dtype

@@ -23,6 +23,7 @@ __all__ = [
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
     "csc_filter_forward", "csc_filter_vjp", "csc_kmeans_loss_grad", "cheb_filter_layer",
     "csc_laplacian_distance", "csc_compressive_cluster", "csc_save_state", "csc_load_state",
+    "csc_splice",
 ]
 
 
@@ -229,6 +230,13 @@ def csc_filter(h, m: int, d: int, p: float, seed: int, k: int = 0, lambda_c: flo
     _check(_lib().csc_filter(h, m, d, p, seed, k, lambda_c, C.byref(lam), C.byref(cnt), C.byref(ev),
                              C.byref(cols)), h, "csc_filter")
     return lam.value, cnt.value, ev.value, cols.value
+
+
+def csc_splice(h, n: int, d: int, p: float, psi_new, lambda_c: float) -> None:
+    """Eq. 6 splice of caller-filtered columns (n x c float32, host or device) into the ring."""
+    ptr, where, _, ld = _arr(psi_new, "psi_out")
+    c = int(psi_new.shape[1])
+    _check(_lib().csc_splice(h, n, d, p, ptr, c, ld or c, where, lambda_c), h, "csc_splice")
 
 
 def csc_get_features(h, dst, normalized: bool = False) -> None:
@@ -522,6 +530,9 @@ class Context:
 
     def filter(self, m, d, p, seed, k=0, lambda_c=-1.0):
         return csc_filter(self.h, m, d, p, seed, k, lambda_c)
+
+    def splice(self, n, d, p, psi_new, lambda_c):
+        return csc_splice(self.h, n, d, p, psi_new, lambda_c)
 
     def get_features(self, dst, normalized=False):
         csc_get_features(self.h, dst, normalized)

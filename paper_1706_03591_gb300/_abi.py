@@ -89,6 +89,7 @@ SIGNATURES = {
     "csc_get_moments": (_i32, [_p, _pd, _i32]),
     "csc_cluster": (_i32, [_p, _i32, _u64, _p, _p, _i32, _pd, _pi]),
     "csc_filter_batched": (_i32, [_p, _i32, _p, _i32, _pd]),
+    "csc_splice": (_i32, [_p, _i64, _i32, _dbl, _p, _i32, _i64, _i32, _dbl]),
     "csc_cheb_filter_noalloc": (_i32, [_i64, _i64, _p, _p, _p, _i32, _dbl, _p, _i32, _i64, _p, _i64,
                                        _pd, _p]),
     "csc_filter_forward": (_i32, [_p, _i32, _pd, _p, _i32, _i64, _p, _i64, _i32]),

@@ -669,6 +669,62 @@ csc_status csc_estimate_lambda_k(csc_ctx* ctx, int k, int m, int d, uint64_t see
   return CSC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Ring slots that the new columns of this snapshot overwrite (Eq. 6 reading): all d at the
+// first snapshot or when p == 0, else the dq = d - floor(p d) slots with the oldest stamp,
+// ties to the lowest slot, in ascending slot order.
+std::vector<int> new_slots(const csc_ctx* ctx, int d, double p) {
+  std::vector<int> slots;
+  if (ctx->t == 0 || p <= 0.0) {
+    for (int q = 0; q < d; ++q) slots.push_back(q);
+    return slots;
+  }
+  const int dp = (int)std::floor(p * d);
+  const int c = d - dp;
+  std::vector<int> order(d);
+  for (int q = 0; q < d; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ctx->stamp[x] < ctx->stamp[y]; });
+  slots.assign(order.begin(), order.begin() + c);
+  std::sort(slots.begin(), slots.end());
+  return slots;
+}
+
+// Writes the new columns psi (device float32, n x c, leading dimension ldp; column v goes to
+// slots[v]) into Theta_t, row-normalises it into Y and advances the ring (Eq. 6, Algorithm 1).
+csc_status splice_columns(csc_ctx* ctx, int64_t n, int d, const std::vector<int>& slots, const float* psi,
+                          int64_t ldp, double lam) {
+  cudaStream_t s = ctx->stream;
+  const int c = (int)slots.size();
+  if (ctx->t == 0) {
+    ALLOC_OK(csc::ensure(ctx->theta, (size_t)n * d * 4));
+    ALLOC_OK(csc::ensure(ctx->y, (size_t)n * d * 4));
+    ALLOC_OK(csc::ensure(ctx->slot_src, (size_t)d * 4));
+    ctx->stamp.assign(d, 0);
+    ctx->ring_n = n;
+    ctx->ring_d = d;
+  }
+  std::vector<int> src_of(d, -1);
+  for (int v = 0; v < c; ++v) src_of[slots[v]] = v;
+  CUDA_OK(cudaMemcpyAsync(ctx->slot_src.ptr, src_of.data(), d * 4, cudaMemcpyHostToDevice, s));
+  CUDA_OK(csc::launch_assemble(csc::as<float>(ctx->theta), d, psi, ldp, csc::as<int>(ctx->slot_src), d,
+                               ctx->y.ptr, ctx->opts.precision, d, n, s));
+  ctx->launches += 1;
+  CUDA_OK(cudaStreamSynchronize(s));
+  ctx->t += 1;
+  for (int q : slots) ctx->stamp[q] = ctx->t;
+  ctx->next_id += c;
+  ctx->lambda = lam;
+  ctx->has_lambda = true;
+  return CSC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k, double lambda_c,
                       double* lambda_out, double* count_out, int* evals_out, int* cols_out) {
   if (!ctx) return CSC_EINVAL;
@@ -682,21 +738,7 @@ csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k
     return fail(ctx, CSC_ESTATE, "csc_filter: the graph's n differs from the feature ring's");
   if (lambda_c < 0 && !ctx->has_lambda && k < 1)
     return fail(ctx, CSC_ESTATE, "csc_filter: no cutoff yet; pass lambda_c >= 0 or k >= 1");
-  cudaStream_t s = ctx->stream;
-  const bool first = ctx->t == 0 || p <= 0.0;
-  std::vector<int> slots;
-  if (first) {
-    for (int q = 0; q < d; ++q) slots.push_back(q);
-  } else {
-    const int dp = (int)std::floor(p * d);
-    const int c = d - dp;
-    std::vector<int> order(d);
-    for (int q = 0; q < d; ++q) order[q] = q;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return ctx->stamp[x] < ctx->stamp[y]; });
-    slots.assign(order.begin(), order.begin() + c);
-    std::sort(slots.begin(), slots.end());
-  }
+  const std::vector<int> slots = new_slots(ctx, d, p);
   const int c = (int)slots.size();
   Source src;
   src.seed = seed;
@@ -734,32 +776,36 @@ csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k
     cnt = cnt2;
   }
   // splice the new columns into the oldest slots and row-normalise (Eq. 6)
-  if (ctx->t == 0) {
-    ALLOC_OK(csc::ensure(ctx->theta, (size_t)n * d * 4));
-    ALLOC_OK(csc::ensure(ctx->y, (size_t)n * d * 4));
-    ALLOC_OK(csc::ensure(ctx->slot_src, (size_t)d * 4));
-    ctx->stamp.assign(d, 0);
-    ctx->ring_n = n;
-    ctx->ring_d = d;
-  }
-  std::vector<int> src_of(d, -1);
-  for (int v = 0; v < c; ++v) src_of[slots[v]] = v;
-  CUDA_OK(cudaMemcpyAsync(ctx->slot_src.ptr, src_of.data(), d * 4, cudaMemcpyHostToDevice, s));
-  CUDA_OK(csc::launch_assemble(csc::as<float>(ctx->theta), d, csc::as<float>(ctx->psi), cpad,
-                               csc::as<int>(ctx->slot_src), d, ctx->y.ptr, ctx->opts.precision, d, n,
-                               s));
-  ctx->launches += 1;
-  CUDA_OK(cudaStreamSynchronize(s));
-  ctx->t += 1;
-  for (int q : slots) ctx->stamp[q] = ctx->t;
-  ctx->next_id += c;
-  ctx->lambda = lam;
-  ctx->has_lambda = true;
+  st = splice_columns(ctx, n, d, slots, csc::as<float>(ctx->psi), cpad, lam);
+  if (st != CSC_OK) return st;
   if (lambda_out) *lambda_out = lam;
   if (count_out) *count_out = cnt;
   if (evals_out) *evals_out = evals;
   if (cols_out) *cols_out = c;
   return CSC_OK;
+}
+
+csc_status csc_splice(csc_ctx* ctx, int64_t n, int d, double p, const float* psi_new, int c, int64_t ldp,
+                      int where, double lambda_c) {
+  if (!ctx) return CSC_EINVAL;
+  if (n < 1 || d < 1 || d > 1024 || !(p >= 0.0 && p < 1.0) || c < 1 || !psi_new || ldp < c ||
+      !valid_where(where) || !(lambda_c >= 0.0 && lambda_c <= 2.0))
+    return fail(ctx, CSC_EINVAL, "csc_splice: bad arguments");
+  if (ctx->t > 0 && (d != ctx->ring_d || n != ctx->ring_n))
+    return fail(ctx, CSC_EINVAL, "csc_splice: n and d must stay the same across snapshots");
+  const std::vector<int> slots = new_slots(ctx, d, p);
+  if ((int)slots.size() != c)
+    return fail(ctx, CSC_EINVAL, "csc_splice: c must be d at the first snapshot (or p = 0), else d - floor(p d)");
+  const float* src = psi_new;
+  int64_t ld = ldp;
+  if (where == CSC_HOST) {
+    ALLOC_OK(csc::ensure(ctx->psi, (size_t)n * c * 4));
+    CUDA_OK(cudaMemcpy2DAsync(ctx->psi.ptr, (size_t)c * 4, psi_new, (size_t)ldp * 4, (size_t)c * 4, n,
+                              cudaMemcpyHostToDevice, ctx->stream));
+    src = csc::as<float>(ctx->psi);
+    ld = c;
+  }
+  return splice_columns(ctx, n, d, slots, src, ld, lambda_c);
 }
 
 csc_status csc_get_features(csc_ctx* ctx, void* dst, int dtype, int64_t ld, int normalized, int where) {
