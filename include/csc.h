@@ -231,6 +231,38 @@ csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k
 csc_status csc_splice(csc_ctx* ctx, int64_t n, int d, double p, const float* psi_new, int c, int64_t ldp,
                       int where, double lambda_c);
 
+/* Edge-similarity policy for the dynamic scheme (Section 4: Definition 4.1, Theorem 4.1 with
+ * Corollary 4.2, Section 4.1).  Given rho_t = ||L_t - L_{t-1}||_F (csc_laplacian_distance):
+ *  - reuse fraction: Corollary 4.2 bounds ||H_t - H_{t-1}||_F by gamma = sqrt(2) rho_t / alpha
+ *    (alpha: the caller's eigengap estimate), and the proof of Theorem 4.1 bounds the added
+ *    k-means cost of reusing p d columns by 2 sqrt(p (1 + delta)) gamma; with delta = 1 and a
+ *    budget eps, p_t = min(p_max, eps^2 / (8 gamma^2)) and dp = floor(p_t d) (dp = 0 refilters
+ *    all d columns).  budget <= 0 or rho_t = 0 keeps p_max.
+ *  - eigencount check: by Weyl's inequality no eigenvalue of L moves by more than the sum of
+ *    rho since the last check, so while that sum stays <= rho_skip the previous cutoff is kept
+ *    without the check; otherwise the check and refinement of Algorithm 1 run and the sum
+ *    restarts at 0.  rho_skip = 0 checks at every snapshot that changed. */
+typedef struct csc_similarity_policy {
+  double alpha;    /* eigengap estimate (> 0 when budget > 0) */
+  double budget;   /* tolerated added k-means cost eps (<= 0: no limit on the reuse) */
+  double rho_skip; /* skip the check while the summed rho since the last one is <= this (>= 0) */
+} csc_similarity_policy;
+
+/* Host-only: the policy's decision for one snapshot: dp_out = reused columns, check_out = 1 when
+ * the eigencount check runs, rho_since_out = the summed rho carried to the next snapshot (0 after
+ * a check).  Errors: CSC_EINVAL. */
+csc_status csc_reuse_policy(int d, double p_max, double rho, const csc_similarity_policy* pol, double rho_since,
+                            int* dp_out, int* check_out, double* rho_since_out);
+
+/* csc_filter with the edge-similarity policy above: at the first snapshot the same as csc_filter
+ * with lambda_c < 0; afterwards dp and the check come from csc_reuse_policy with rho (this
+ * snapshot's distance to the previous graph) and the sum carried on the context.  k >= 1.
+ * Outputs as csc_filter (evals 0 when the check was skipped), checked_out = whether the check
+ * ran (may be NULL).  Errors as csc_filter. */
+csc_status csc_filter_adaptive(csc_ctx* ctx, int m, int d, double p_max, uint64_t seed, int k, double rho,
+                               const csc_similarity_policy* pol, double* lambda_out, double* count_out,
+                               int* evals_out, int* cols_out, int* checked_out);
+
 /* Copies Theta_t (normalized = 0, float32 ring in slot order) or the row-normalised
  * features y_i = theta_i / ||theta_i|| (normalized = 1) into dst (n x d, dtype
  * CSC_F32 or CSC_BF16, leading dimension ld >= d, host or device per where). */

@@ -27,6 +27,22 @@ Readings beyond the paper's text:
   assignment (Lloyd, see oracle.kmeans).
 * Column g of the signal block is the Philox stream of global column id g;
   ids are handed out in order (0..d-1 at t = 1, then dq per snapshot).
+
+Edge-similarity policy (optional; Section 4, Definition 4.1, Theorem 4.1, Corollary 4.2), with
+rho_t = ||L_t - L_{t-1}||_F given per snapshot:
+
+* Reuse fraction.  The proof of Theorem 4.1 bounds the error of the reused columns by
+  ||(Psi_t - Psi_{t-1}) S||_F <= sqrt(p (1 + delta)) ||H_t - H_{t-1}||_F, and the k-means cost
+  by twice that; Corollary 4.2 bounds ||H_t - H_{t-1}||_F by gamma = sqrt(2) rho_t / alpha for
+  an eigengap alpha.  (The theorem's statement writes the term as (1 + delta) p gamma; the
+  reading follows the proof.)  With delta = 1 and a budget eps on the added cost,
+  2 sqrt(2 p) gamma <= eps gives p_t = min(p_max, eps^2 / (8 gamma^2)); dp_t = floor(p_t d), and
+  dp_t = 0 refilters all d columns.  eps <= 0 or rho_t = 0 keeps p_max.
+* Eigencount check.  Weyl's inequality gives |lambda_i(L_t) - lambda_i(L_s)| <= ||L_t - L_s||_2
+  <= sum of rho since snapshot s, so while the sum of rho since the last check stays <= rho_skip
+  the previous cutoff is kept without the check (Section 4.1: recompute lambda_k from time to
+  time only); otherwise the check (and refinement) of Algorithm 1 runs and the sum restarts.
+  rho_skip = 0 keeps Algorithm 1's check at every snapshot with rho_t > 0.
 """
 from __future__ import annotations
 
@@ -50,6 +66,20 @@ def row_normalize(theta: np.ndarray) -> np.ndarray:
     return out
 
 
+def reuse_policy(d: int, p_max: float, rho: float, alpha: float, budget: float, rho_skip: float,
+                 rho_since: float) -> tuple[int, bool, float]:
+    """(dp, run the eigencount check, rho summed since the last check) for one snapshot under the
+    edge-similarity policy of the module header."""
+    acc = rho_since + rho
+    p = p_max
+    if budget > 0.0 and rho > 0.0:
+        gamma = math.sqrt(2.0) * rho / alpha
+        p = min(p_max, budget * budget / (8.0 * gamma * gamma))
+    dp = int(math.floor(p * d))
+    check = not (acc <= rho_skip)
+    return dp, check, (0.0 if check else acc)
+
+
 def oldest_slots(stamp: np.ndarray, count: int) -> np.ndarray:
     """The `count` slots with the smallest stamp, ties to the lowest slot, ascending slot order."""
     order = np.lexsort((np.arange(stamp.size), stamp))
@@ -69,16 +99,24 @@ class DynamicCSC:
         self.next_id = 0
         self.lam = None
         self.labels = None
+        self.rho_since = 0.0
         self.history: list[dict] = []
 
-    def step(self, row_ptr, col_idx, vals=None, init_idx=None) -> np.ndarray:
+    def step(self, row_ptr, col_idx, vals=None, init_idx=None, rho=None, policy=None) -> np.ndarray:
+        """One snapshot.  With ``policy`` = dict(alpha, budget, rho_skip) and ``rho`` =
+        ||L_t - L_{t-1}||_F the edge-similarity policy of the module header sets dp and whether
+        the eigencount check runs (from the second snapshot on)."""
         self.t += 1
         n, d, k, m = self.n, self.d, self.k, self.m
         lt = lp.shifted_laplacian(n, row_ptr, col_idx, vals)
-        if self.t == 1 or self.p <= 0.0:
+        check = True
+        dp = int(math.floor(self.p * d)) if self.p > 0.0 else 0
+        if policy is not None and self.t > 1:
+            dp, check, self.rho_since = reuse_policy(d, self.p, rho, policy["alpha"], policy["budget"],
+                                                     policy["rho_skip"], self.rho_since)
+        if self.t == 1 or dp == 0:
             slots = np.arange(d)
         else:
-            dp = int(math.floor(self.p * d))
             slots = oldest_slots(self.stamp, d - dp)
         c = slots.size
         ids = np.arange(self.next_id, self.next_id + c)
@@ -89,7 +127,10 @@ class DynamicCSC:
             return cb.eigencount(cb.combine(basis, cb.filter_coefficients(m, lam)), d)
 
         tau = self.tau_fixed if self.tau_fixed is not None else cb.count_tolerance(k, c)
-        lam, cnt, evals = cb.lambda_search(count_fn, k, tau, self.lam, self.max_bisect)
+        if check or self.lam is None:
+            lam, cnt, evals = cb.lambda_search(count_fn, k, tau, self.lam, self.max_bisect)
+        else:
+            lam, cnt, evals = self.lam, count_fn(self.lam), 0
         psi = cb.combine(basis, cb.filter_coefficients(m, lam))
         self.theta[:, slots] = psi
         self.stamp[slots] = self.t
@@ -104,7 +145,7 @@ class DynamicCSC:
             c0 = km.warm_centroids(y, self.labels, init_idx)
         labels, cents, passes, conv = km.lloyd(y, c0, self.max_iter)
         self.labels = labels
-        self.history.append(dict(t=self.t, lam=lam, count=cnt, evals=evals, c=c, slots=slots,
+        self.history.append(dict(t=self.t, lam=lam, count=cnt, evals=evals, c=c, slots=slots, checked=check,
                                  passes=passes, converged=conv,
                                  inertia=km.inertia(y, labels, cents)))
         return labels

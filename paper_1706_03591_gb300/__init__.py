@@ -23,7 +23,7 @@ __all__ = [
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
     "csc_filter_forward", "csc_filter_vjp", "csc_kmeans_loss_grad", "cheb_filter_layer",
     "csc_laplacian_distance", "csc_compressive_cluster", "csc_save_state", "csc_load_state",
-    "csc_splice",
+    "csc_splice", "csc_reuse_policy", "csc_filter_adaptive",
 ]
 
 
@@ -230,6 +230,31 @@ def csc_filter(h, m: int, d: int, p: float, seed: int, k: int = 0, lambda_c: flo
     _check(_lib().csc_filter(h, m, d, p, seed, k, lambda_c, C.byref(lam), C.byref(cnt), C.byref(ev),
                              C.byref(cols)), h, "csc_filter")
     return lam.value, cnt.value, ev.value, cols.value
+
+
+def _policy(alpha: float, budget: float, rho_skip: float):
+    return _abi.csc_similarity_policy(float(alpha), float(budget), float(rho_skip))
+
+
+def csc_reuse_policy(d: int, p_max: float, rho: float, alpha: float, budget: float, rho_skip: float,
+                     rho_since: float = 0.0):
+    """Host-only decision of the edge-similarity policy: (dp, check, rho summed since the check)."""
+    pol = _policy(alpha, budget, rho_skip)
+    dp, ck, acc = C.c_int(), C.c_int(), C.c_double()
+    _check(_lib().csc_reuse_policy(d, p_max, rho, C.byref(pol), rho_since, C.byref(dp), C.byref(ck),
+                                   C.byref(acc)))
+    return dp.value, bool(ck.value), acc.value
+
+
+def csc_filter_adaptive(h, m: int, d: int, p_max: float, seed: int, k: int, rho: float, alpha: float,
+                        budget: float, rho_skip: float):
+    """csc_filter under the edge-similarity policy; returns (lambda_c, count, evaluations,
+    columns filtered, check ran)."""
+    pol = _policy(alpha, budget, rho_skip)
+    lam, cnt, ev, cols, ck = C.c_double(), C.c_double(), C.c_int(), C.c_int(), C.c_int()
+    _check(_lib().csc_filter_adaptive(h, m, d, p_max, seed, k, rho, C.byref(pol), C.byref(lam), C.byref(cnt),
+                                      C.byref(ev), C.byref(cols), C.byref(ck)), h, "csc_filter_adaptive")
+    return lam.value, cnt.value, ev.value, cols.value, bool(ck.value)
 
 
 def csc_splice(h, n: int, d: int, p: float, psi_new, lambda_c: float) -> None:
@@ -530,6 +555,9 @@ class Context:
 
     def filter(self, m, d, p, seed, k=0, lambda_c=-1.0):
         return csc_filter(self.h, m, d, p, seed, k, lambda_c)
+
+    def filter_adaptive(self, m, d, p_max, seed, k, rho, alpha, budget, rho_skip=0.0):
+        return csc_filter_adaptive(self.h, m, d, p_max, seed, k, rho, alpha, budget, rho_skip)
 
     def splice(self, n, d, p, psi_new, lambda_c):
         return csc_splice(self.h, n, d, p, psi_new, lambda_c)

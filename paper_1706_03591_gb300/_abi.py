@@ -44,6 +44,10 @@ class csc_stats(C.Structure):
     ]
 
 
+class csc_similarity_policy(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("budget", C.c_double), ("rho_skip", C.c_double)]
+
+
 class csc_graph_desc(C.Structure):
     _fields_ = [
         ("n", C.c_int64),
@@ -89,6 +93,8 @@ SIGNATURES = {
     "csc_get_moments": (_i32, [_p, _pd, _i32]),
     "csc_cluster": (_i32, [_p, _i32, _u64, _p, _p, _i32, _pd, _pi]),
     "csc_filter_batched": (_i32, [_p, _i32, _p, _i32, _pd]),
+    "csc_reuse_policy": (_i32, [_i32, _dbl, _dbl, _p, _dbl, _pi, _pi, _pd]),
+    "csc_filter_adaptive": (_i32, [_p, _i32, _i32, _dbl, _u64, _i32, _dbl, _p, _pd, _pd, _pi, _pi, _pi]),
     "csc_splice": (_i32, [_p, _i64, _i32, _dbl, _p, _i32, _i64, _i32, _dbl]),
     "csc_cheb_filter_noalloc": (_i32, [_i64, _i64, _p, _p, _p, _i32, _dbl, _p, _i32, _i64, _p, _i64,
                                        _pd, _p]),

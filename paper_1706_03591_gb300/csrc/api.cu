@@ -674,15 +674,14 @@ csc_status csc_estimate_lambda_k(csc_ctx* ctx, int k, int m, int d, uint64_t see
 namespace {
 
 // Ring slots that the new columns of this snapshot overwrite (Eq. 6 reading): all d at the
-// first snapshot or when p == 0, else the dq = d - floor(p d) slots with the oldest stamp,
-// ties to the lowest slot, in ascending slot order.
-std::vector<int> new_slots(const csc_ctx* ctx, int d, double p) {
+// first snapshot or when dp == 0, else the dq = d - dp slots with the oldest stamp, ties to the
+// lowest slot, in ascending slot order.
+std::vector<int> new_slots(const csc_ctx* ctx, int d, int dp) {
   std::vector<int> slots;
-  if (ctx->t == 0 || p <= 0.0) {
+  if (ctx->t == 0 || dp <= 0) {
     for (int q = 0; q < d; ++q) slots.push_back(q);
     return slots;
   }
-  const int dp = (int)std::floor(p * d);
   const int c = d - dp;
   std::vector<int> order(d);
   for (int q = 0; q < d; ++q) order[q] = q;
@@ -725,20 +724,18 @@ csc_status splice_columns(csc_ctx* ctx, int64_t n, int d, const std::vector<int>
 
 extern "C" {
 
-csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k, double lambda_c,
-                      double* lambda_out, double* count_out, int* evals_out, int* cols_out) {
-  if (!ctx) return CSC_EINVAL;
-  if (!ctx->g.loaded) return fail(ctx, CSC_ESTATE, "csc_filter: no graph loaded");
-  if (m < 1 || d < 1 || d > 1024 || !(p >= 0.0 && p < 1.0) || lambda_c > 2.0)
-    return fail(ctx, CSC_EINVAL, "csc_filter: need m >= 1, 1 <= d <= 1024, 0 <= p < 1, lambda_c <= 2");
+}  // extern "C"
+
+namespace {
+
+// One snapshot of Algorithm 1 up to the clustering with dp reused columns; check = false keeps
+// the current cutoff without the eigencount check.
+csc_status filter_snapshot(csc_ctx* ctx, int m, int d, int dp, uint64_t seed, int k, double lambda_c,
+                           bool check, double* lambda_out, double* count_out, int* evals_out,
+                           int* cols_out) {
   const int64_t n = ctx->g.n;
-  if (ctx->t > 0 && d != ctx->ring_d)
-    return fail(ctx, CSC_EINVAL, "csc_filter: d must stay the same across snapshots");
-  if (ctx->t > 0 && n != ctx->ring_n)
-    return fail(ctx, CSC_ESTATE, "csc_filter: the graph's n differs from the feature ring's");
-  if (lambda_c < 0 && !ctx->has_lambda && k < 1)
-    return fail(ctx, CSC_ESTATE, "csc_filter: no cutoff yet; pass lambda_c >= 0 or k >= 1");
-  const std::vector<int> slots = new_slots(ctx, d, p);
+  if (!check && ctx->has_lambda && lambda_c < 0) lambda_c = ctx->lambda;
+  const std::vector<int> slots = new_slots(ctx, d, dp);
   const int c = (int)slots.size();
   Source src;
   src.seed = seed;
@@ -785,6 +782,77 @@ csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k
   return CSC_OK;
 }
 
+csc_status filter_args(csc_ctx* ctx, int m, int d, double p, int k, double lambda_c, const char* who) {
+  if (!ctx->g.loaded) return fail(ctx, CSC_ESTATE, std::string(who) + ": no graph loaded");
+  if (m < 1 || d < 1 || d > 1024 || !(p >= 0.0 && p < 1.0) || lambda_c > 2.0)
+    return fail(ctx, CSC_EINVAL, std::string(who) + ": need m >= 1, 1 <= d <= 1024, 0 <= p < 1, lambda_c <= 2");
+  if (ctx->t > 0 && d != ctx->ring_d)
+    return fail(ctx, CSC_EINVAL, std::string(who) + ": d must stay the same across snapshots");
+  if (ctx->t > 0 && ctx->g.n != ctx->ring_n)
+    return fail(ctx, CSC_ESTATE, std::string(who) + ": the graph's n differs from the feature ring's");
+  if (lambda_c < 0 && !ctx->has_lambda && k < 1)
+    return fail(ctx, CSC_ESTATE, std::string(who) + ": no cutoff yet; pass lambda_c >= 0 or k >= 1");
+  return CSC_OK;
+}
+
+// Edge-similarity policy (Definition 4.1, Theorem 4.1 with Corollary 4.2; rule in csc.h).
+void reuse_policy(int d, double p_max, double rho, const csc_similarity_policy& pol, double rho_since, int* dp,
+                  int* check, double* rho_after) {
+  const double acc = rho_since + rho;
+  double p = p_max;
+  if (pol.budget > 0.0 && rho > 0.0) {
+    const double gamma = std::sqrt(2.0) * rho / pol.alpha;
+    p = std::min(p_max, pol.budget * pol.budget / (8.0 * gamma * gamma));
+  }
+  *dp = (int)std::floor(p * d);
+  *check = !(acc <= pol.rho_skip);
+  *rho_after = *check ? 0.0 : acc;
+}
+
+bool valid_policy(const csc_similarity_policy* pol) {
+  return pol && pol->budget == pol->budget && pol->rho_skip >= 0.0 && (pol->budget <= 0.0 || pol->alpha > 0.0);
+}
+
+}  // namespace
+
+extern "C" {
+
+csc_status csc_filter(csc_ctx* ctx, int m, int d, double p, uint64_t seed, int k, double lambda_c,
+                      double* lambda_out, double* count_out, int* evals_out, int* cols_out) {
+  if (!ctx) return CSC_EINVAL;
+  csc_status st = filter_args(ctx, m, d, p, k, lambda_c, "csc_filter");
+  if (st != CSC_OK) return st;
+  const int dp = p > 0.0 ? (int)std::floor(p * d) : 0;
+  return filter_snapshot(ctx, m, d, dp, seed, k, lambda_c, true, lambda_out, count_out, evals_out, cols_out);
+}
+
+csc_status csc_reuse_policy(int d, double p_max, double rho, const csc_similarity_policy* pol, double rho_since,
+                            int* dp_out, int* check_out, double* rho_since_out) {
+  if (d < 1 || !(p_max >= 0.0 && p_max < 1.0) || !(rho >= 0.0) || !(rho_since >= 0.0) || !valid_policy(pol) ||
+      !dp_out || !check_out || !rho_since_out)
+    return CSC_EINVAL;
+  reuse_policy(d, p_max, rho, *pol, rho_since, dp_out, check_out, rho_since_out);
+  return CSC_OK;
+}
+
+csc_status csc_filter_adaptive(csc_ctx* ctx, int m, int d, double p_max, uint64_t seed, int k, double rho,
+                               const csc_similarity_policy* pol, double* lambda_out, double* count_out,
+                               int* evals_out, int* cols_out, int* checked_out) {
+  if (!ctx) return CSC_EINVAL;
+  if (!valid_policy(pol) || !(rho >= 0.0) || k < 1)
+    return fail(ctx, CSC_EINVAL, "csc_filter_adaptive: need k >= 1, rho >= 0 and a valid policy");
+  csc_status st = filter_args(ctx, m, d, p_max, k, -1.0, "csc_filter_adaptive");
+  if (st != CSC_OK) return st;
+  int dp = p_max > 0.0 ? (int)std::floor(p_max * d) : 0, check = 1;
+  double after = 0.0;
+  if (ctx->t > 0) reuse_policy(d, p_max, rho, *pol, ctx->rho_since, &dp, &check, &after);
+  st = filter_snapshot(ctx, m, d, dp, seed, k, -1.0, check != 0, lambda_out, count_out, evals_out, cols_out);
+  if (st != CSC_OK) return st;
+  ctx->rho_since = after;
+  if (checked_out) *checked_out = check;
+  return CSC_OK;
+}
+
 csc_status csc_splice(csc_ctx* ctx, int64_t n, int d, double p, const float* psi_new, int c, int64_t ldp,
                       int where, double lambda_c) {
   if (!ctx) return CSC_EINVAL;
@@ -793,7 +861,7 @@ csc_status csc_splice(csc_ctx* ctx, int64_t n, int d, double p, const float* psi
     return fail(ctx, CSC_EINVAL, "csc_splice: bad arguments");
   if (ctx->t > 0 && (d != ctx->ring_d || n != ctx->ring_n))
     return fail(ctx, CSC_EINVAL, "csc_splice: n and d must stay the same across snapshots");
-  const std::vector<int> slots = new_slots(ctx, d, p);
+  const std::vector<int> slots = new_slots(ctx, d, p > 0.0 ? (int)std::floor(p * d) : 0);
   if ((int)slots.size() != c)
     return fail(ctx, CSC_EINVAL, "csc_splice: c must be d at the first snapshot (or p = 0), else d - floor(p d)");
   const float* src = psi_new;

@@ -304,6 +304,7 @@ struct csc_ctx {
   int64_t next_id = 0;
   bool has_lambda = false;
   double lambda = 0.0;
+  double rho_since = 0.0;  // edge distance summed since the last eigencount check
   // k-means
   csc::KmeansState km;
   csc::DevBuf prev_assign;

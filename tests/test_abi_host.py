@@ -125,3 +125,21 @@ def test_binding_rejects_wrong_element_types():
     assert code == csc.CSC_BF16
     with pytest.raises(TypeError, match="psi_out"):
         csc._arr(torch.zeros((4, 3), dtype=torch.bfloat16), "psi_out")
+
+
+def test_similarity_policy_matches_oracle(lib):
+    """csc_reuse_policy makes the decision of oracle.dynamic.reuse_policy, bit for bit."""
+    from oracle.dynamic import reuse_policy
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        d = int(rng.integers(1, 300))
+        p_max = float(rng.uniform(0, 0.99))
+        rho = float(rng.choice([0.0, rng.exponential(2.0)]))
+        alpha = float(rng.uniform(0.01, 0.5))
+        budget = float(rng.choice([0.0, rng.uniform(0.1, 200.0)]))
+        rho_skip = float(rng.choice([0.0, rng.uniform(0, 5)]))
+        since = float(rng.uniform(0, 3))
+        assert lib.csc_reuse_policy(d, p_max, rho, alpha, budget, rho_skip, since) == \
+            reuse_policy(d, p_max, rho, alpha, budget, rho_skip, since)
+    with pytest.raises(lib.CscError):
+        lib.csc_reuse_policy(10, 0.5, 1.0, 0.0, 1.0, 0.0)  # alpha must be positive with a budget

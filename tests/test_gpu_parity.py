@@ -15,6 +15,7 @@ from conftest import fp32_floor
 from oracle import chebyshev as cb
 from oracle import kmeans as km
 from oracle import laplacian as lp
+from oracle import similarity as sm
 from oracle.dynamic import DynamicCSC, row_normalize
 from oracle.philox import gaussian_columns
 
@@ -435,3 +436,45 @@ def test_errors_and_call_order(gpu_lib):
             ctx.set_graph(3, dev(np.array([0, 1, 2, 2], dtype=np.int64)),
                           dev(np.array([5, 0], dtype=np.int32)))  # column out of range
         assert "malformed" in ctx.last_error
+
+
+def test_algorithm1_similarity_policy_parity(gpu_lib):
+    """Algorithm 1 under the edge-similarity policy (csc_filter_adaptive, Theorem 4.1 with
+    Corollary 4.2 and Weyl's inequality) over a sequence that alternates node reassignment plus
+    edge redrawing (Section 5.2) with light edge redrawing.  The GPU computes rho_t itself
+    (csc_laplacian_distance); reuse counts, skipped checks and cutoffs equal the oracle's,
+    features within the float32 tolerance, assignments exact."""
+    n, k, d, m, p_max, seed = 2000, 10, 64, 50, 0.75, 77
+    policy = dict(alpha=0.1, budget=100.0, rho_skip=2.0)
+    graphs = [W.sbm_graph(n, k, 20, 10, seed=1)]
+    for t in range(6):
+        graphs.append(W.sbm_perturb(graphs[-1], 0.01, 0.03, seed=400 + t) if t % 2 == 0
+                      else W.edge_redraw(graphs[-1], 0.005, seed=400 + t))
+    oracle = DynamicCSC(n, k, d, p_max, m, seed)
+    cols_seen, checks_seen = set(), set()
+    with gpu_lib.Context() as ctx:
+        assign = torch.zeros(n, dtype=torch.int32, device="cuda")
+        prev = None
+        for t, g in enumerate(graphs):
+            cur = (dev(g.row_ptr), dev(g.col_idx), None)
+            rho = 0.0 if prev is None else ctx.laplacian_distance(n, prev, cur)
+            rho_ref = 0.0 if t == 0 else sm.laplacian_distance(
+                n, (graphs[t - 1].row_ptr, graphs[t - 1].col_idx, None), (g.row_ptr, g.col_idx, None))
+            assert rho == pytest.approx(rho_ref, rel=1e-10)
+            idx = W.forgy_indices(n, k, seed=600 + t)
+            lab_ref = oracle.step(g.row_ptr, g.col_idx, init_idx=idx, rho=rho_ref, policy=policy)
+            h = oracle.history[-1]
+            ctx.set_graph(n, cur[0], cur[1])
+            lam, cnt, ev, cols, checked = ctx.filter_adaptive(m, d, p_max, seed, k, rho, **policy)
+            ctx.cluster(k, seed, idx, assign)
+            assert cols == h["c"] and checked == h["checked"], (t, cols, checked, h)
+            assert lam == h["lam"] and ev == h["evals"], (t, lam, ev, h)
+            theta = np.zeros((n, d), dtype=np.float32)
+            ctx.get_features(theta)
+            assert rel(theta, oracle.features()) < FP32_TOL
+            np.testing.assert_array_equal(assign.cpu().numpy(), lab_ref)
+            cols_seen.add(cols)
+            checks_seen.add(checked)
+            prev = cur
+    # the sequence exercised a reduced reuse, full reuse and both check outcomes
+    assert len(cols_seen) >= 3 and checks_seen == {True, False}
