@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 4
+#define CSC_ABI_VERSION 5
 
 typedef struct csc_ctx csc_ctx;
 
@@ -74,6 +74,12 @@ typedef struct csc_opts {
   int estimator;    /* eigencount of the cutoff search: 0 = (d/c) ||h(L) R||_F^2, which
                        estimates tr h(L)^2 (default); 1 = (d/c) tr(R^T h(L) R), which
                        estimates tr h(L) (Hutchinson) */
+  int reorder;      /* 1 (default): the library stores the graph in its own node order,
+                       degrees descending (ties by node id), so that the rows a block of the
+                       recursion handles have similar degrees and the most gathered rows are
+                       contiguous; the order is fixed at the first csc_set_graph of a feature
+                       ring and every row-indexed input and output of the ABI stays in the
+                       caller's node order.  0: the caller's order. */
 } csc_opts;
 
 /* Counters of a context (csc_get_stats). */
@@ -392,15 +398,17 @@ csc_status csc_laplacian_distance(csc_ctx* ctx, int64_t n, const int64_t* rp_a, 
  * assignment X_{t-1} from one snapshot to the next.  csc_save_state writes that state to a
  * binary file at path: the ring (Theta float32 n x d and its row-normalised copy in the
  * context's precision), the ring stamps, the snapshot counter, the next signal column id,
- * the cutoff, the moments of the last filtering and the previous assignment with its k.
- * csc_load_state reads it into a context created with the same precision, replacing that
- * context's dynamic state; the graph is not part of the state, and the next csc_set_graph must
- * have the saved n.  A resumed context continues the sequence exactly as the saving one
- * would have: the same signal columns, slots, cutoff check and warm start.
- * The file is written in the machine's byte order: magic "CSCSTATE", version 1.
+ * the cutoff, the moments of the last filtering, the previous assignment with its k, the edge
+ * distance summed since the last eigencount check (csc_filter_adaptive) and the context's node
+ * order (csc_opts.reorder; the ring's rows are stored in it).  csc_load_state reads it into a
+ * context created with the same precision and reorder setting, replacing that context's dynamic
+ * state; the graph is not part of the state, so csc_set_graph (with the saved n) must come before
+ * the next filtering.  A resumed context continues the sequence exactly as the saving one would
+ * have: the same signal columns, slots, cutoff check and warm start.
+ * The file is written in the machine's byte order: magic "CSCSTATE", version 2.
  * Errors: CSC_ESTATE (save before any csc_filter), CSC_EINVAL (NULL path, a file that cannot
- * be opened, written or read, not a state file, a corrupt or truncated file, a precision
- * mismatch), CSC_ENOMEM, CSC_ECUDA. */
+ * be opened, written or read, not a state file, a corrupt or truncated file, a precision or
+ * reorder mismatch), CSC_ENOMEM, CSC_ECUDA. */
 csc_status csc_save_state(csc_ctx* ctx, const char* path);
 csc_status csc_load_state(csc_ctx* ctx, const char* path);
 

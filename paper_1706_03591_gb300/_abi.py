@@ -25,6 +25,7 @@ class csc_opts(C.Structure):
         ("checked", C.c_int),
         ("timing", C.c_int),
         ("estimator", C.c_int),
+        ("reorder", C.c_int),
     ]
 
 

@@ -212,8 +212,9 @@ struct Source {
   int64_t ldr = 0;
 };
 
-// Chebyshev recursion over c columns in tiles.  psi_dst: device float, leading dim ldp
-// (nullptr: moments only).  Fills ctx->mu (2m+1 trace moments).
+// Chebyshev recursion over c columns in tiles.  The signal source is in the caller's node order;
+// psi_dst (device float, leading dim ldp; nullptr: moments only) receives Psi in the internal
+// node order.  Fills ctx->mu (2m+1 trace moments).
 csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source& src, float* psi_dst,
                       int64_t ldp) {
   const int64_t n = ctx->g.n;
@@ -246,11 +247,13 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
   for (int tile = 0; tile < ntiles; ++tile) {
     const int c0 = tile * w;
     const int valid = std::min(w, c - c0);
+    // signals and caller blocks are in the caller's node order; the tile in the internal order
+    const int32_t* to_caller = ctx->g.permuted ? csc::as<int32_t>(ctx->g.perm) : nullptr;
     if (src.philox)
       CUDA_OK(csc::launch_signals(ctx->tbuf[0].ptr, t0_dtype, n, w, w, src.seed, src.col0 + c0, valid,
-                                  inv_sqrt_d, s));
+                                  inv_sqrt_d, s, to_caller));
     else
-      CUDA_OK(csc::launch_copy_tile(ctx->tbuf[0].ptr, src.R, t0_dtype, n, w, src.ldr, c0, valid, s));
+      CUDA_OK(csc::launch_copy_tile(ctx->tbuf[0].ptr, src.R, t0_dtype, n, w, src.ldr, c0, valid, s, to_caller));
     double* tile_part = part + (size_t)tile * rows * grid;
     csc::StepArgs sa{};
     sa.n = n;
@@ -262,6 +265,8 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
     sa.ivs = csc::as<float>(ctx->g.ivs);
     sa.blk_row = csc::as<int32_t>(ctx->g.blk_row);
     sa.nblk = csc::edge_blocks(ctx->g.nnz);
+    sa.srow = csc::as<int32_t>(ctx->g.srow);
+    sa.nsblk = csc::row_blocks(ctx->g.n, ctx->g.nnz);
     sa.psi = psi_dst ? psi_dst + c0 : nullptr;
     sa.ldp = ldp;
     sa.coef = csc::as<float>(ctx->coef);
@@ -324,6 +329,23 @@ size_t dtype_size(int dtype) { return dtype == CSC_BF16 ? 2 : 4; }
 bool valid_dtype(int dtype) { return dtype == CSC_F32 || dtype == CSC_BF16; }
 bool valid_where(int where) { return where == CSC_HOST || where == CSC_DEVICE; }
 
+// Node order of the internal graph: degrees descending, ties by caller id (a stable counting
+// sort, O(n + max degree)).  perm[i] = caller row of internal row i, iperm its inverse.
+void degree_order(int64_t n, const int64_t* rp, std::vector<int32_t>& perm, std::vector<int32_t>& iperm) {
+  int64_t maxdeg = 0;
+  for (int64_t u = 0; u < n; ++u) maxdeg = std::max(maxdeg, rp[u + 1] - rp[u]);
+  std::vector<int64_t> start(maxdeg + 2, 0);
+  for (int64_t u = 0; u < n; ++u) start[maxdeg - (rp[u + 1] - rp[u]) + 1] += 1;
+  for (int64_t b = 1; b <= maxdeg + 1; ++b) start[b] += start[b - 1];
+  perm.assign(n, 0);
+  iperm.assign(n, 0);
+  for (int64_t u = 0; u < n; ++u) {
+    const int64_t i = start[maxdeg - (rp[u + 1] - rp[u])]++;
+    perm[i] = (int32_t)u;
+    iperm[u] = (int32_t)i;
+  }
+}
+
 csc_status validate_host_csr(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rp,
                              const int32_t* ci, const float* vals) {
   if (rp[0] != 0 || rp[n] != nnz) return fail(ctx, CSC_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] = nnz");
@@ -343,17 +365,21 @@ csc_status validate_host_csr(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t
 }
 
 // Copies an n x d device block (dtype src_dtype, ld_src) to a caller destination.
+// Caller row u -> internal row (nullptr when the graph is in the caller's order).
+const int32_t* to_internal(csc_ctx* ctx) { return ctx->g.permuted ? csc::as<int32_t>(ctx->g.iperm) : nullptr; }
+
+// Row i of dst is row src_row[i] of src (src_row nullptr: row i).
 csc_status copy_out(csc_ctx* ctx, const void* src, int src_dtype, int64_t ld_src, int64_t n, int d,
-                    void* dst, int dst_dtype, int64_t ld_dst, int where) {
+                    void* dst, int dst_dtype, int64_t ld_dst, int where, const int32_t* src_row = nullptr) {
   cudaStream_t s = ctx->stream;
   const size_t esz = dtype_size(dst_dtype);
   ctx->launches += 1;
   if (where == CSC_DEVICE) {
-    CUDA_OK(csc::launch_convert(src, src_dtype, ld_src, dst, dst_dtype, ld_dst, n, d, s));
+    CUDA_OK(csc::launch_convert(src, src_dtype, ld_src, dst, dst_dtype, ld_dst, n, d, s, src_row));
     return CSC_OK;
   }
   ALLOC_OK(csc::ensure(ctx->out_stage, (size_t)std::max<int64_t>(n, 1) * d * esz));
-  CUDA_OK(csc::launch_convert(src, src_dtype, ld_src, ctx->out_stage.ptr, dst_dtype, d, n, d, s));
+  CUDA_OK(csc::launch_convert(src, src_dtype, ld_src, ctx->out_stage.ptr, dst_dtype, d, n, d, s, src_row));
   if (n > 0 && d > 0)
     CUDA_OK(cudaMemcpy2DAsync(dst, ld_dst * esz, ctx->out_stage.ptr, d * esz, d * esz, n,
                               cudaMemcpyDeviceToHost, s));
@@ -368,7 +394,7 @@ csc_status copy_out(csc_ctx* ctx, const void* src, int src_dtype, int64_t ld_src
 namespace {
 
 constexpr char kStateMagic[8] = {'C', 'S', 'C', 'S', 'T', 'A', 'T', 'E'};
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 
 struct StateFile {
   FILE* f = nullptr;
@@ -394,6 +420,7 @@ void csc_default_opts(csc_opts* o) {
   o->checked = 0;
   o->timing = 0;
   o->estimator = 0;
+  o->reorder = 1;
 }
 
 const char* csc_status_string(csc_status s) {
@@ -418,7 +445,8 @@ csc_status csc_create(csc_ctx** out, const csc_opts* opts, void* cuda_stream) {
   csc_default_opts(&o);
   if (opts) o = *opts;
   if (!valid_dtype(o.precision) || o.max_bisect < 1 || o.max_iter < 1 ||
-      (o.col_tile != 0 && !valid_tile(o.col_tile)) || (o.estimator != 0 && o.estimator != 1))
+      (o.col_tile != 0 && !valid_tile(o.col_tile)) || (o.estimator != 0 && o.estimator != 1) ||
+      (o.reorder != 0 && o.reorder != 1))
     return CSC_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -441,7 +469,8 @@ void csc_destroy(csc_ctx* ctx) {
   if (ctx->b_exec) cudaGraphExecDestroy(ctx->b_exec);
   if (ctx->b_cap) cudaStreamDestroy(ctx->b_cap);
   DevBuf* bufs[] = {&ctx->g.row_ptr, &ctx->g.col, &ctx->g.val, &ctx->g.scale, &ctx->g.deg,
-                    &ctx->g.blk_row, &ctx->g.vs, &ctx->g.ivs,
+                    &ctx->g.blk_row, &ctx->g.srow, &ctx->g.vs, &ctx->g.ivs,
+                    &ctx->g.perm, &ctx->g.iperm, &ctx->g.urp, &ctx->g.ucol, &ctx->g.uval, &ctx->gtmp,
                     &ctx->tbuf[0], &ctx->tbuf[1], &ctx->tbuf[2], &ctx->psi, &ctx->part, &ctx->ef,
                     &ctx->coef, &ctx->rstage, &ctx->theta, &ctx->y, &ctx->slot_src,
                     &ctx->prev_assign, &ctx->ystage, &ctx->astage, &ctx->out_stage, &ctx->bad,
@@ -450,7 +479,8 @@ void csc_destroy(csc_ctx* ctx) {
                     &ctx->b_waves, &ctx->b_work,
                     &ctx->gs.coef_f, &ctx->gs.ckpt, &ctx->gs.seg, &ctx->gs.rt, &ctx->gs.gt,
                     &ctx->gs.phi[0], &ctx->gs.phi[1], &ctx->gs.phi[2], &ctx->gs.H, &ctx->gs.tpos,
-                    &ctx->gs.nsum, &ctx->gs.part, &ctx->gs.flag, &ctx->gs.ga, &ctx->gs.rcopy, &ctx->sim};
+                    &ctx->gs.nsum, &ctx->gs.part, &ctx->gs.flag, &ctx->gs.ga, &ctx->gs.rcopy, &ctx->gs.gw_stage,
+                    &ctx->sim};
   for (DevBuf* b : bufs) csc::release(*b);
   csc::kmeans_release(ctx->km);
   csc::compressive_release(ctx->cmp);
@@ -490,35 +520,52 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
     return fail(ctx, CSC_EINVAL, "csc_set_graph: the vertex set is fixed across snapshots");
   cudaStream_t s = ctx->stream;
   csc::Graph& g = ctx->g;
+  const bool reorder = ctx->opts.reorder != 0;
+  // caller CSR: uploaded into the caller-order buffers when the library reorders, else in place
+  csc::DevBuf& rp_b = reorder ? g.urp : g.row_ptr;
+  csc::DevBuf& col_b = reorder ? g.ucol : g.col;
+  csc::DevBuf& val_b = reorder ? g.uval : g.val;
   ALLOC_OK(csc::ensure(g.row_ptr, (size_t)(n + 1) * 8));
   ALLOC_OK(csc::ensure(g.col, (size_t)nnz * 4));
+  ALLOC_OK(csc::ensure(rp_b, (size_t)(n + 1) * 8));
+  ALLOC_OK(csc::ensure(col_b, (size_t)nnz * 4));
   ALLOC_OK(csc::ensure(g.scale, (size_t)n * 4));
   ALLOC_OK(csc::ensure(g.vs, (size_t)n * 4));
   ALLOC_OK(csc::ensure(g.ivs, (size_t)n * 4));
   ALLOC_OK(csc::ensure(g.deg, (size_t)n * 8));
   ALLOC_OK(csc::ensure(g.blk_row, ((size_t)csc::edge_blocks(nnz) + 1) * 4));
+  ALLOC_OK(csc::ensure(g.srow, ((size_t)csc::row_blocks(n, nnz) + 1) * 4));
   const cudaMemcpyKind kind = where == CSC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CUDA_OK(cudaMemcpyAsync(g.row_ptr.ptr, row_ptr, (size_t)(n + 1) * 8, kind, s));
-  if (nnz > 0) CUDA_OK(cudaMemcpyAsync(g.col.ptr, col_idx, (size_t)nnz * 4, kind, s));
+  CUDA_OK(cudaMemcpyAsync(rp_b.ptr, row_ptr, (size_t)(n + 1) * 8, kind, s));
+  if (nnz > 0) CUDA_OK(cudaMemcpyAsync(col_b.ptr, col_idx, (size_t)nnz * 4, kind, s));
   g.weighted = vals != nullptr;
   if (g.weighted) {
     ALLOC_OK(csc::ensure(g.val, (size_t)nnz * 4));
-    if (nnz > 0) CUDA_OK(cudaMemcpyAsync(g.val.ptr, vals, (size_t)nnz * 4, kind, s));
+    ALLOC_OK(csc::ensure(val_b, (size_t)nnz * 4));
+    if (nnz > 0) CUDA_OK(cudaMemcpyAsync(val_b.ptr, vals, (size_t)nnz * 4, kind, s));
   }
   g.n = n;
   g.nnz = nnz;
   // host input is always validated, on the device after the upload (an O(nnz) pass on the host
   // would cost more than the copy); the host validator runs only to name a failure
   if (where == CSC_HOST || ctx->opts.checked) {
+    csc::Graph view;  // the caller's CSR
+    view.n = n;
+    view.nnz = nnz;
+    view.weighted = g.weighted;
+    view.row_ptr.ptr = rp_b.ptr;
+    view.col.ptr = col_b.ptr;
+    view.val.ptr = g.weighted ? val_b.ptr : nullptr;
     ALLOC_OK(csc::ensure(ctx->bad, 16));
     CUDA_OK(cudaMemsetAsync(ctx->bad.ptr, 0, 8, s));
-    CUDA_OK(csc::launch_graph_check(g, csc::as<unsigned long long>(ctx->bad), s));
+    CUDA_OK(csc::launch_graph_check(view, csc::as<unsigned long long>(ctx->bad), s));
+    view.row_ptr.ptr = view.col.ptr = view.val.ptr = nullptr;  // not owned
     ctx->launches += 1;
     unsigned long long bad = 0;
     int64_t ends[2] = {0, 0};
     CUDA_OK(cudaMemcpyAsync(&bad, ctx->bad.ptr, 8, cudaMemcpyDeviceToHost, s));
-    CUDA_OK(cudaMemcpyAsync(&ends[0], g.row_ptr.ptr, 8, cudaMemcpyDeviceToHost, s));
-    CUDA_OK(cudaMemcpyAsync(&ends[1], csc::as<int64_t>(g.row_ptr) + n, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(&ends[0], rp_b.ptr, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(&ends[1], csc::as<int64_t>(rp_b) + n, 8, cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
     if (bad != 0 || ends[0] != 0 || ends[1] != nnz) {
       g.loaded = false;
@@ -529,6 +576,32 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
       return fail(ctx, CSC_EINVAL, "csc_set_graph: malformed CSR (" + std::to_string(bad) +
                                        " violations)");
     }
+  }
+  if (reorder) {
+    // the node order: fixed while a feature ring exists (its rows are stored in that order)
+    if (!(ctx->t > 0 && g.permuted && (int64_t)g.h_perm.size() == n)) {
+      std::vector<int64_t> rp_host;
+      const int64_t* rp = row_ptr;
+      if (where == CSC_DEVICE) {
+        rp_host.resize(n + 1);
+        CUDA_OK(cudaMemcpyAsync(rp_host.data(), row_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaStreamSynchronize(s));
+        rp = rp_host.data();
+      }
+      degree_order(n, rp, g.h_perm, g.h_iperm);
+      ALLOC_OK(csc::ensure(g.perm, (size_t)n * 4));
+      ALLOC_OK(csc::ensure(g.iperm, (size_t)n * 4));
+      CUDA_OK(cudaMemcpyAsync(g.perm.ptr, g.h_perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+      CUDA_OK(cudaMemcpyAsync(g.iperm.ptr, g.h_iperm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+      CUDA_OK(cudaStreamSynchronize(s));  // the host vectors may be reallocated later
+    }
+    ALLOC_OK(csc::ensure(ctx->gtmp, ((size_t)n + (size_t)csc::scan_sums_len(n)) * 8));
+    long long* tmp = csc::as<long long>(ctx->gtmp);
+    CUDA_OK(csc::launch_permute_graph(g, tmp, tmp + n, s));
+    ctx->launches += 4;
+    g.permuted = true;
+  } else {
+    g.permuted = false;
   }
   CUDA_OK(csc::launch_graph_prep(g, s));
   CUDA_OK(csc::launch_block_rows(g, s));
@@ -637,8 +710,8 @@ csc_status csc_cheb_filter(csc_ctx* ctx, int m, double lambda_c, const void* R, 
   csc_status st = run_filter(ctx, m, lambda_c, c, src, psi, cpad);
   if (st != CSC_OK) return st;
   if (psi_out) {
-    const cudaMemcpyKind kind = psi_where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    CUDA_OK(cudaMemcpy2DAsync(psi_out, ldp * 4, psi, (size_t)cpad * 4, (size_t)c * 4, n, kind, s));
+    st = copy_out(ctx, psi, CSC_F32, cpad, n, c, psi_out, CSC_F32, ldp, psi_where, to_internal(ctx));
+    if (st != CSC_OK) return st;
     CUDA_OK(cudaStreamSynchronize(s));
   }
   if (mu_out) std::copy(ctx->mu.begin(), ctx->mu.end(), mu_out);
@@ -867,9 +940,19 @@ csc_status csc_splice(csc_ctx* ctx, int64_t n, int d, double p, const float* psi
   const float* src = psi_new;
   int64_t ld = ldp;
   if (where == CSC_HOST) {
-    ALLOC_OK(csc::ensure(ctx->psi, (size_t)n * c * 4));
-    CUDA_OK(cudaMemcpy2DAsync(ctx->psi.ptr, (size_t)c * 4, psi_new, (size_t)ldp * 4, (size_t)c * 4, n,
+    ALLOC_OK(csc::ensure(ctx->rstage, (size_t)n * c * 4));
+    CUDA_OK(cudaMemcpy2DAsync(ctx->rstage.ptr, (size_t)c * 4, psi_new, (size_t)ldp * 4, (size_t)c * 4, n,
                               cudaMemcpyHostToDevice, ctx->stream));
+    src = csc::as<float>(ctx->rstage);
+    ld = c;
+  }
+  if (ctx->g.permuted) {
+    // the caller's rows into the internal node order of the ring
+    if (!ctx->g.loaded || ctx->g.n != n) return fail(ctx, CSC_ESTATE, "csc_splice: load the snapshot's graph first");
+    ALLOC_OK(csc::ensure(ctx->psi, (size_t)n * c * 4));
+    CUDA_OK(csc::launch_convert(src, CSC_F32, ld, ctx->psi.ptr, CSC_F32, c, n, c, ctx->stream,
+                                csc::as<int32_t>(ctx->g.perm)));
+    ctx->launches += 1;
     src = csc::as<float>(ctx->psi);
     ld = c;
   }
@@ -883,9 +966,9 @@ csc_status csc_get_features(csc_ctx* ctx, void* dst, int dtype, int64_t ld, int 
     return fail(ctx, CSC_EINVAL, "csc_get_features: bad arguments");
   if (normalized)
     return copy_out(ctx, ctx->y.ptr, ctx->opts.precision, ctx->ring_d, ctx->ring_n, ctx->ring_d, dst,
-                    dtype, ld, where);
+                    dtype, ld, where, to_internal(ctx));
   return copy_out(ctx, ctx->theta.ptr, CSC_F32, ctx->ring_d, ctx->ring_n, ctx->ring_d, dst, dtype, ld,
-                  where);
+                  where, to_internal(ctx));
 }
 
 csc_status csc_get_moments(csc_ctx* ctx, double* mu_out, int len) {
@@ -965,6 +1048,10 @@ csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_i
     idx = forgy_draw(seed ^ ((uint64_t)ctx->t * 0x9E3779B97F4A7C15ull), n, k);
   }
   cudaStream_t s = ctx->stream;
+  // the ring is in the internal node order; Forgy rows and the assignment are in the caller's
+  const bool perm = ctx->g.permuted;
+  if (perm)
+    for (int64_t& v : idx) v = ctx->g.h_iperm[v];
   const bool warm = ctx->has_prev && ctx->prev_k == k;
   csc::KmeansResult res;
   csc_status st = csc::kmeans_run(ctx->km, ctx->y.ptr, ctx->opts.precision, n, d, d, k, idx.data(),
@@ -976,8 +1063,14 @@ csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_i
   if (st != CSC_OK) return st;
   ALLOC_OK(csc::ensure(ctx->prev_assign, (size_t)n * 4));
   CUDA_OK(cudaMemcpyAsync(ctx->prev_assign.ptr, res.assign, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  const int32_t* out = res.assign;
+  if (perm) {
+    ALLOC_OK(csc::ensure(ctx->astage, (size_t)n * 4));
+    CUDA_OK(csc::launch_gather_i32(csc::as<int32_t>(ctx->astage), res.assign, csc::as<int32_t>(ctx->g.iperm), n, s));
+    out = csc::as<int32_t>(ctx->astage);
+  }
   const cudaMemcpyKind kind = where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  CUDA_OK(cudaMemcpyAsync(assign_out, res.assign, (size_t)n * 4, kind, s));
+  CUDA_OK(cudaMemcpyAsync(assign_out, out, (size_t)n * 4, kind, s));
   CUDA_OK(cudaStreamSynchronize(s));
   ctx->has_prev = true;
   ctx->prev_k = k;
@@ -1010,6 +1103,17 @@ csc_status csc_compressive_cluster(csc_ctx* ctx, const float* theta, const void*
     y_dtype = ctx->opts.precision;
     d = ctx->ring_d;
     ld = d;
+    if (ctx->g.permuted) {
+      // the draws are defined in the caller's node order: the ring's rows in that order first
+      const size_t esz = dtype_size(y_dtype);
+      ALLOC_OK(csc::ensure(cs.theta_stage, (size_t)n * d * 4));
+      ALLOC_OK(csc::ensure(cs.y_stage, (size_t)n * d * esz));
+      CUDA_OK(csc::launch_convert(th, CSC_F32, d, cs.theta_stage.ptr, CSC_F32, d, n, d, s, to_internal(ctx)));
+      CUDA_OK(csc::launch_convert(yy, y_dtype, d, cs.y_stage.ptr, y_dtype, d, n, d, s, to_internal(ctx)));
+      ctx->launches += 2;
+      th = csc::as<float>(cs.theta_stage);
+      yy = cs.y_stage.ptr;
+    }
     if (lambda_c < 0.0) {
       if (!ctx->has_lambda) return fail(ctx, CSC_ESTATE, "csc_compressive_cluster: no cutoff yet");
       lambda_c = ctx->lambda;
@@ -1096,13 +1200,21 @@ csc_status csc_compressive_cluster(csc_ctx* ctx, const float* theta, const void*
   if (st != CSC_OK) return st;
   CUDA_OK(csc::compressive_argmax(csc::as<float>(cs.x), cpad, n, k, csc::as<int32_t>(cs.assign), s));
   ctx->launches += 1;
-
+  // X and its argmax are in the internal node order
+  const int32_t* assign = csc::as<int32_t>(cs.assign);
+  if (ctx->g.permuted) {
+    ALLOC_OK(csc::ensure(ctx->astage, (size_t)n * 4));
+    CUDA_OK(csc::launch_gather_i32(csc::as<int32_t>(ctx->astage), assign, to_internal(ctx), n, s));
+    assign = csc::as<int32_t>(ctx->astage);
+  }
   const cudaMemcpyKind kind = out_where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  CUDA_OK(cudaMemcpyAsync(assign_out, cs.assign.ptr, (size_t)n * 4, kind, s));
+  CUDA_OK(cudaMemcpyAsync(assign_out, assign, (size_t)n * 4, kind, s));
   if (sample_out) CUDA_OK(cudaMemcpyAsync(sample_out, omega, (size_t)n_omega * 4, kind, s));
   if (sample_labels_out) CUDA_OK(cudaMemcpyAsync(sample_labels_out, labels, (size_t)n_omega * 4, kind, s));
-  if (interp_out)
-    CUDA_OK(cudaMemcpy2DAsync(interp_out, (size_t)ldx * 4, cs.x.ptr, (size_t)cpad * 4, (size_t)k * 4, n, kind, s));
+  if (interp_out) {
+    st = copy_out(ctx, cs.x.ptr, CSC_F32, cpad, n, k, interp_out, CSC_F32, ldx, out_where, to_internal(ctx));
+    if (st != CSC_OK) return st;
+  }
   CUDA_OK(cudaStreamSynchronize(s));
   if (n_sampled_out) *n_sampled_out = n_omega;
   if (restart_out) *restart_out = pick;
@@ -1136,13 +1248,16 @@ csc_status csc_save_state(csc_ctx* ctx, const char* path) {
   const int32_t last_m = ctx->last_m, n_mu = (int32_t)ctx->mu.size();
   const int32_t has_prev = ctx->has_prev ? 1 : 0, prev_k = ctx->prev_k;
   const int64_t t = ctx->t, next_id = ctx->next_id;
+  // the ring's rows are stored in the context's node order, which is saved with them
+  const int32_t permuted = ctx->g.permuted && (int64_t)ctx->g.h_perm.size() == n ? 1 : 0;
   const bool ok = put(sf.f, kStateMagic, 8) && put(sf.f, &kStateVersion, 4) && put(sf.f, &precision, 4) &&
                   put(sf.f, &n, 8) && put(sf.f, &ring_d, 4) && put(sf.f, &t, 8) && put(sf.f, &next_id, 8) &&
                   put(sf.f, &has_lambda, 4) && put(sf.f, &ctx->lambda, 8) && put(sf.f, &last_m, 4) &&
                   put(sf.f, &n_mu, 4) && put(sf.f, ctx->mu.data(), ctx->mu.size() * 8) &&
                   put(sf.f, ctx->stamp.data(), ctx->stamp.size() * 8) && put(sf.f, &has_prev, 4) &&
                   put(sf.f, &prev_k, 4) && put(sf.f, theta.data(), cells * 4) && put(sf.f, y.data(), y.size()) &&
-                  put(sf.f, prev.data(), prev.size() * 4);
+                  put(sf.f, prev.data(), prev.size() * 4) && put(sf.f, &ctx->rho_since, 8) &&
+                  put(sf.f, &permuted, 4) && put(sf.f, ctx->g.h_perm.data(), permuted ? (size_t)n * 4 : 0);
   const bool closed = fclose(sf.f) == 0;
   sf.f = nullptr;
   if (!ok || !closed) return fail(ctx, CSC_EINVAL, std::string("csc_save_state: write failed for ") + path);
@@ -1182,8 +1297,21 @@ csc_status csc_load_state(csc_ctx* ctx, const char* path) {
   std::vector<float> theta(cells);
   std::vector<unsigned char> y(cells * ysz);
   std::vector<int32_t> prev(has_prev ? (size_t)n : 0);
-  ok = get(sf.f, theta.data(), cells * 4) && get(sf.f, y.data(), y.size()) && get(sf.f, prev.data(), prev.size() * 4);
-  if (!ok) return fail(ctx, CSC_EINVAL, "csc_load_state: truncated file");
+  double rho_since = 0.0;
+  int32_t permuted = 0;
+  ok = get(sf.f, theta.data(), cells * 4) && get(sf.f, y.data(), y.size()) && get(sf.f, prev.data(), prev.size() * 4) &&
+       get(sf.f, &rho_since, 8) && get(sf.f, &permuted, 4);
+  if (!ok || (permuted != 0 && permuted != 1) || !(rho_since >= 0.0))
+    return fail(ctx, CSC_EINVAL, "csc_load_state: truncated file");
+  if ((permuted != 0) != (ctx->opts.reorder != 0))
+    return fail(ctx, CSC_EINVAL, "csc_load_state: the state was saved with another reorder setting");
+  std::vector<int32_t> perm(permuted ? (size_t)n : 0), iperm(perm.size(), -1);
+  if (!get(sf.f, perm.data(), perm.size() * 4)) return fail(ctx, CSC_EINVAL, "csc_load_state: truncated file");
+  for (size_t i = 0; i < perm.size(); ++i) {
+    const int32_t u = perm[i];
+    if (u < 0 || u >= n || iperm[u] != -1) return fail(ctx, CSC_EINVAL, "csc_load_state: corrupt node order");
+    iperm[u] = (int32_t)i;
+  }
   for (int32_t v : prev)
     if (v < 0 || v >= prev_k) return fail(ctx, CSC_EINVAL, "csc_load_state: assignment label out of range");
   cudaStream_t s = ctx->stream;
@@ -1194,7 +1322,19 @@ csc_status csc_load_state(csc_ctx* ctx, const char* path) {
   CUDA_OK(cudaMemcpyAsync(ctx->theta.ptr, theta.data(), cells * 4, cudaMemcpyHostToDevice, s));
   CUDA_OK(cudaMemcpyAsync(ctx->y.ptr, y.data(), y.size(), cudaMemcpyHostToDevice, s));
   if (has_prev) CUDA_OK(cudaMemcpyAsync(ctx->prev_assign.ptr, prev.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  if (permuted) {
+    ALLOC_OK(csc::ensure(ctx->g.perm, (size_t)n * 4));
+    ALLOC_OK(csc::ensure(ctx->g.iperm, (size_t)n * 4));
+    CUDA_OK(cudaMemcpyAsync(ctx->g.perm.ptr, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemcpyAsync(ctx->g.iperm.ptr, iperm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  }
   CUDA_OK(cudaStreamSynchronize(s));
+  // the graph is not part of the state: load the next snapshot before filtering
+  ctx->g.loaded = false;
+  ctx->g.permuted = permuted != 0;
+  ctx->g.h_perm = std::move(perm);
+  ctx->g.h_iperm = std::move(iperm);
+  ctx->rho_since = rho_since;
   ctx->ring_n = n;
   ctx->ring_d = ring_d;
   ctx->t = t;

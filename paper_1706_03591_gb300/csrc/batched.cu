@@ -50,7 +50,7 @@ uint64_t size_class(const csc_graph_desc& g) {
 }
 
 struct GraphPlan {
-  size_t off_scale, off_vs, off_ivs, off_deg, off_blk;  // in b_prep
+  size_t off_scale, off_vs, off_ivs, off_deg, off_blk, off_srow;  // in b_prep
   size_t off_psi;                                        // in b_psi (floats)
   int w, ntiles, cpad, nblk;
 };
@@ -83,6 +83,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     p.off_ivs = prep_bytes; prep_bytes += al(n * 4);
     p.off_deg = prep_bytes; prep_bytes += al(n * 8);
     p.off_blk = prep_bytes; prep_bytes += al(((size_t)p.nblk + 1) * 4);
+    p.off_srow = prep_bytes; prep_bytes += al(((size_t)csc::row_blocks(n, descs[g].nnz) + 1) * 4);
   }
   B_ALLOC(csc::ensure(ctx->b_prep, prep_bytes));
   char* prep = static_cast<char*>(ctx->b_prep.ptr);
@@ -101,6 +102,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     v.ivs.ptr = prep + plan[g].off_ivs;
     v.deg.ptr = prep + plan[g].off_deg;
     v.blk_row.ptr = prep + plan[g].off_blk;
+    v.srow.ptr = prep + plan[g].off_srow;
     B_CUDA(csc::launch_graph_prep(v, s));
     B_CUDA(csc::launch_block_rows(v, s));
     ctx->launches += 2;
@@ -136,6 +138,8 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
       sa.ivs = static_cast<const float*>(views[rep].ivs.ptr);
       sa.blk_row = static_cast<const int32_t*>(views[rep].blk_row.ptr);
       sa.nblk = plan[rep].nblk;
+      sa.srow = static_cast<const int32_t*>(views[rep].srow.ptr);
+      sa.nsblk = csc::row_blocks(d.n, d.nnz);
       sa.w = w;
       sa.tg = tb;
       sa.tp = tb + d.n * w;

@@ -150,52 +150,6 @@ __device__ __forceinline__ bool stage_block(const StepArgs& a, Stage& st, int b,
   return true;
 }
 
-// Row-based blocks of the general step: a CTA processes whole passes of its row slots per
-// block, at most kStepRows rows (the staging barriers then come once per 128 rows on large
-// graphs), fewer on small graphs so that every CTA of the grid gets about two blocks; the
-// block's columns are staged here.
-constexpr int kStepEdgeBuf = 5632;  // keeps StageRows under the 48 KB static limit
-constexpr int kStepRows = 128;
-struct StageRows {
-  int col[kStepEdgeBuf];
-  float wt[kStepEdgeBuf];
-  int rp[kStepRows + 1];
-};
-
-// Stages rows [rs, re): row offsets, columns, and the per-edge weights when the graph is
-// weighted or SCALED (first step: w_uv D^-1/2_v, since T_0 = R is unscaled).
-// Returns false when the edges exceed the buffer (the block then reads global memory).
-template <bool SCALED = false>
-__device__ __forceinline__ bool stage_rows(const StepArgs& a, StageRows& st, int rs, int re) {
-  const int64_t es = __ldg(a.row_ptr + rs);
-  const int64_t ee = __ldg(a.row_ptr + re);
-  if (ee - es > kStepEdgeBuf) return false;
-  for (int i = threadIdx.x; i <= re - rs; i += blockDim.x)
-    st.rp[i] = (int)(__ldcs(a.row_ptr + rs + i) - es);
-  const int ne = (int)(ee - es);
-  const bool weighted = a.val != nullptr;
-  for (int base = 0; base < ne; base += kStageUnroll * blockDim.x) {
-    int c[kStageUnroll];
-    float v[kStageUnroll];
-#pragma unroll
-    for (int u = 0; u < kStageUnroll; ++u) {
-      const int e = base + u * blockDim.x + threadIdx.x;
-      c[u] = e < ne ? __ldcs(a.col + es + e) : 0;
-      v[u] = (e < ne && weighted) ? __ldcs(a.val + es + e) : 1.0f;
-      if (SCALED && e < ne) v[u] *= __ldg(a.scale + c[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < kStageUnroll; ++u) {
-      const int e = base + u * blockDim.x + threadIdx.x;
-      if (e < ne) {
-        st.col[e] = c[u];
-        if (SCALED || weighted) st.wt[e] = v[u];
-      }
-    }
-  }
-  return true;
-}
-
 constexpr int kGatherUnroll = 4;
 
 // sum_{e in row} wt_e X[col_e, 4 columns of this lane], folded over the S neighbour slots.
@@ -366,88 +320,10 @@ __device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const ST& st
   return acc;
 }
 
-// One row block of the first step (row-parallel, as the general step): T_1 = L~ T_0 =
-// -D^-1/2 W D^-1/2 R, stored as V_1 = vs T_1; Psi = a_0 T_0 + a_1 T_1; partials <T_0,T_0>,
-// <T_1,T_1>, <T_1,T_0> accumulated into acc (first lane of each slot).
-template <int LPR, typename T0>
-__device__ __forceinline__ void first_rows(const StepArgs& a, StageRows& st, int b, double (&acc)[3]) {
-  constexpr int S = 32 / LPR;
-  constexpr int kRowsPerPass = (kBlock / 32) * S;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int slot = lane / LPR, sub = lane % LPR;
-  const T0* __restrict__ t0 = static_cast<const T0*>(a.tg);
-  const int w = a.w;
-  float a0 = 0.f, a1 = 0.f;
-  if (a.psi != nullptr) { a0 = __ldg(a.coef); a1 = __ldg(a.coef + 1); }
-  const int rs = b * a.rpb;
-  const int re = (int)min((int64_t)rs + a.rpb, a.n);
-  __syncthreads();
-  const bool staged = stage_rows<true>(a, st, rs, re);
-  __syncthreads();
-  for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
-    const int r = r0 + wid * S + slot;
-    const bool valid = r < re;
-    const int64_t row = valid ? r : rs;
-    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
-    float si = 0.f, vsi = 0.f;
-    if (valid) {
-      own = ld4(t0 + row * w + sub * 4);
-      si = -__ldg(a.scale + row);
-      vsi = __ldg(a.vs + row);
-    }
-    const float4 g = gather_own_row<LPR, StageRows, true, T0>(a, st, staged, t0, row, r - rs, valid, sub);
-    float e0 = 0.f, e1 = 0.f, f1 = 0.f;
-    if (valid) {
-      const float4 t1 = make_float4(si * g.x, si * g.y, si * g.z, si * g.w);
-      st4(a.tn + row * w + sub * 4, make_float4(vsi * t1.x, vsi * t1.y, vsi * t1.z, vsi * t1.w));
-      if (a.psi != nullptr) {
-        float4 p;
-        p.x = fmaf(a1, t1.x, a0 * own.x);
-        p.y = fmaf(a1, t1.y, a0 * own.y);
-        p.z = fmaf(a1, t1.z, a0 * own.z);
-        p.w = fmaf(a1, t1.w, a0 * own.w);
-        st4(a.psi + row * a.ldp + sub * 4, p);
-      }
-      e0 = dot4(own, own);
-      e1 = dot4(t1, t1);
-      f1 = dot4(t1, own);
-    }
-#pragma unroll
-    for (int off = 1; off < LPR; off <<= 1) {
-      e0 += __shfl_xor_sync(kFull, e0, off);
-      e1 += __shfl_xor_sync(kFull, e1, off);
-      f1 += __shfl_xor_sync(kFull, f1, off);
-    }
-    if (sub == 0 && valid) {
-      acc[0] += (double)e0;
-      acc[1] += (double)e1;
-      acc[2] += (double)f1;
-    }
-  }
-}
-
-template <int LPR, typename T0>
-__global__ void __launch_bounds__(kBlock, 4) cheb_first_kernel(StepArgs a) {
-  __shared__ StageRows st;
-  double acc[3] = {0.0, 0.0, 0.0};  // <T0,T0>, <T1,T1>, <T1,T0>
-  const int nb = (int)((a.n + a.rpb - 1) / a.rpb);
-  for (int b = blockIdx.x; b < nb; b += gridDim.x) first_rows<LPR, T0>(a, st, b, acc);
-  // every lane may hold a partial: reduce the warp first
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    acc[0] += __shfl_xor_sync(kFull, acc[0], off);
-    acc[1] += __shfl_xor_sync(kFull, acc[1], off);
-    acc[2] += __shfl_xor_sync(kFull, acc[2], off);
-  }
-  block_store<3>(acc, a.part);
-}
-
-// One block of a general step (row-parallel: the LPR lanes of a slot own a row):
-// V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1}, Psi += a_{j+1} T_{j+1}; partials
-// <T_{j+1},T_{j+1}>, <T_{j+1},T_j> accumulated into acc (first lane of each slot).
-// ST = StageRows: block b is rows [b R, b R + R) with R two full passes of row slots (the
-// standalone step kernel); ST = Stage: block b is edge block b (the persistent batched kernel,
-// whose items are edge blocks, fewer and larger per grid-barrier phase).
+// One edge block of a general step of the persistent batched kernel (row-parallel: the LPR
+// lanes of a slot own a row): V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1},
+// Psi += a_{j+1} T_{j+1}; partials <T_{j+1},T_{j+1}>, <T_{j+1},T_j> accumulated into acc (first
+// lane of each slot).
 template <int LPR, typename TP, typename ST>
 __device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, double (&acc)[2]) {
   constexpr int S = 32 / LPR;
@@ -461,13 +337,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, dou
   int rs, re;
   bool staged;
   __syncthreads();
-  if constexpr (std::is_same<ST, StageRows>::value) {
-    rs = b * a.rpb;
-    re = (int)min((int64_t)rs + a.rpb, a.n);
-    staged = stage_rows(a, st, rs, re);
-  } else {
-    staged = stage_block<false>(a, st, b, rs, re);
-  }
+  staged = stage_block<false>(a, st, b, rs, re);
   __syncthreads();
   for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
     const int r = r0 + wid * S + slot;
@@ -519,20 +389,344 @@ __device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, dou
   }
 }
 
-template <int LPR, typename TP>
-// Four CTAs per SM (at most 64 registers per thread) keep more gathers in flight.
-__global__ void __launch_bounds__(kBlock, 4) cheb_step_kernel(StepArgs a) {
-  __shared__ StageRows st;
-  double acc[2] = {0.0, 0.0};  // <T_{j+1},T_{j+1}>, <T_{j+1},T_j>
-  const int nb = (int)((a.n + a.rpb - 1) / a.rpb);
-  for (int b = blockIdx.x; b < nb; b += gridDim.x) step_block<LPR, TP>(a, st, b, acc);
+// ------------------------------------------------------------------ standalone step kernels
+//
+// One launch per step and column tile.  The rows are cut into blocks of about kBlockWeight
+// units, a row weighing its stored edges plus kRowCost (g.srow, built at set_graph), so that
+// every block carries about the same gather and stream work whatever the degree distribution.
+// A CTA walks its blocks in chunks: one coalesced load of the row offsets (one per thread) finds
+// the longest run of rows whose edges fit the shared-memory buffer, and their column indices
+// and edge weights are staged there.  Each row of a chunk is reduced by spr slots of LPR lanes
+// (spr a power of two chosen from the chunk's largest degree, so that a long row spreads over
+// up to a whole warp while short rows keep one slot each); the slots stride over the row's
+// edges with kRowUnroll 16-byte loads in flight per lane and are folded with xor shuffles in a
+// fixed order.  A row too long for the buffer on its own (a hub) is reduced by the whole CTA
+// straight from global memory: every slot of every warp strides over its edges, the warps
+// fold their slots, and the first warp adds the warp sums in warp order.  The gathered block
+// T_j is read-only during a launch, so its rows are loaded through the non-coherent L1 path,
+// which keeps hub rows that many rows share in L1.
+
+constexpr int kChunkRows = kBlock - 1;  // at most one row offset per thread
+constexpr int kChunkEdges = 5632;       // staged columns and weights: 45 KB
+constexpr int kEdgesPerSlot = 32;       // spr: smallest power of two with spr * 32 >= max degree
+
+struct StageChunk {
+  union {
+    struct {
+      int col[kChunkEdges];
+      float wt[kChunkEdges];
+    } e;
+    float4 red[kBlock / 32][32];  // cooperative rows: the warps' partial sums
+  } u;
+  int rp[kChunkRows + 1];
+  int64_t base;
+  int maxdeg;
+};
+
+// Gathered-row loads through L1 (ld.global.nc).
+__device__ __forceinline__ float4 ldg_row(const float* ptr) { return __ldg(reinterpret_cast<const float4*>(ptr)); }
+__device__ __forceinline__ float4 ldg_row(const __nv_bfloat16* ptr) {
+  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(ptr));
+  const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+  const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+  return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+// Stages the longest run of rows [r, r + rows) of a block ending at re whose edges fit the
+// buffer (at most kChunkRows rows): row offsets relative to st.base, the largest degree, the
+// column indices and the edge weights (w_e, times D^-1/2[col_e] when SCALED).  Returns rows;
+// 0 when row r alone exceeds the buffer.  Block-uniform; starts with a barrier that protects
+// the previous chunk's shared data.
+template <bool SCALED>
+__device__ __forceinline__ int stage_chunk(const StepArgs& a, StageChunk& st, int r, int re) {
+  const int lim = min(kChunkRows, re - r);
+  const bool have = (int)threadIdx.x <= lim;
+  int64_t off = 0;
+  __syncthreads();
+  if (have) off = __ldg(a.row_ptr + r + threadIdx.x);
+  if (threadIdx.x == 0) {
+    st.base = off;
+    st.maxdeg = 0;
+  }
+  __syncthreads();
+  const int64_t base = st.base;
+  // row_ptr is non-decreasing, so the offsets that fit form a prefix
+  const int cnt = __syncthreads_count(have && off - base <= kChunkEdges);
+  const int rows = cnt - 1;
+  if (rows == 0) return 0;
+  if ((int)threadIdx.x < cnt) st.rp[threadIdx.x] = (int)(off - base);
+  __syncthreads();
+  const int ne = st.rp[rows];
+  int deg = (int)threadIdx.x < rows ? st.rp[threadIdx.x + 1] - st.rp[threadIdx.x] : 0;
+  deg = __reduce_max_sync(kFull, deg);
+  if ((threadIdx.x & 31) == 0 && deg > 0) atomicMax(&st.maxdeg, deg);
+  const bool weighted = a.val != nullptr;
+  for (int b0 = 0; b0 < ne; b0 += kStageUnroll * kBlock) {
+    int c[kStageUnroll];
+    float v[kStageUnroll];
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int e = b0 + u * kBlock + threadIdx.x;
+      c[u] = e < ne ? __ldcs(a.col + base + e) : 0;
+      v[u] = (e < ne && weighted) ? __ldcs(a.val + base + e) : 1.0f;
+      if (SCALED && e < ne) v[u] *= __ldg(a.scale + c[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kStageUnroll; ++u) {
+      const int e = b0 + u * kBlock + threadIdx.x;
+      if (e < ne) {
+        st.u.e.col[e] = c[u];
+        if (SCALED || weighted) st.u.e.wt[e] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  return rows;
+}
+
+// Epilogue of one row (the LPR lanes of its first slot, 4 columns each): FIRST: T_1 = -S^2... in
+// the stored form V_1 = vs T_1 with T_1 = -D^-1/2 g, Psi = a_0 T_0 + a_1 T_1, dots <T0,T0>,
+// <T1,T1>, <T1,T0>; else V_{j+1} = -2 vs^2 g - V_{j-1}, Psi += a_{j+1} T_{j+1}, dots
+// <T_{j+1},T_{j+1}>, <T_{j+1},T_j>.  own: T_0 (FIRST) or V_j; prev: V_{j-1} (T_0 when
+// tp_unscaled); p: the Psi row.
+template <bool FIRST>
+__device__ __forceinline__ void row_epilogue(const StepArgs& a, int64_t row, int sub, float4 g, float4 own,
+                                             float4 prev, float4 p, float c0, float c1, float sc, float vsi,
+                                             float ivsi, float (&dots)[3]) {
+  const int w = a.w;
+  if constexpr (FIRST) {
+    const float4 t1 = make_float4(sc * g.x, sc * g.y, sc * g.z, sc * g.w);
+    st4(a.tn + row * w + sub * 4, make_float4(vsi * t1.x, vsi * t1.y, vsi * t1.z, vsi * t1.w));
+    if (a.psi != nullptr) {
+      float4 q;
+      q.x = fmaf(c1, t1.x, c0 * own.x);
+      q.y = fmaf(c1, t1.y, c0 * own.y);
+      q.z = fmaf(c1, t1.z, c0 * own.z);
+      q.w = fmaf(c1, t1.w, c0 * own.w);
+      st4(a.psi + row * a.ldp + sub * 4, q);
+    }
+    dots[0] = dot4(own, own);
+    dots[1] = dot4(t1, t1);
+    dots[2] = dot4(t1, own);
+  } else {
+    const float c2 = -2.0f * vsi * vsi;
+    if (a.tp_unscaled) { prev.x *= vsi; prev.y *= vsi; prev.z *= vsi; prev.w *= vsi; }
+    float4 v;
+    v.x = fmaf(c2, g.x, -prev.x);
+    v.y = fmaf(c2, g.y, -prev.y);
+    v.z = fmaf(c2, g.z, -prev.z);
+    v.w = fmaf(c2, g.w, -prev.w);
+    st4(a.tn + row * w + sub * 4, v);
+    const float4 t = make_float4(v.x * ivsi, v.y * ivsi, v.z * ivsi, v.w * ivsi);
+    const float4 tc = make_float4(own.x * ivsi, own.y * ivsi, own.z * ivsi, own.w * ivsi);
+    if (a.psi != nullptr) {
+      p.x = fmaf(c1, t.x, p.x);
+      p.y = fmaf(c1, t.y, p.y);
+      p.z = fmaf(c1, t.z, p.z);
+      p.w = fmaf(c1, t.w, p.w);
+      st4h(a.psi + row * a.ldp + sub * 4, p, l2_stream());
+    }
+    dots[0] = dot4(t, t);
+    dots[1] = dot4(t, tc);
+    dots[2] = 0.f;
+  }
+}
+
+// Own-row operands of a row, issued before its gather.
+template <bool FIRST, typename TG, typename TP>
+__device__ __forceinline__ void row_operands(const StepArgs& a, int64_t row, int sub, float4& own,
+                                             float4& prev, float4& p, float& sc, float& vsi, float& ivsi) {
+  const uint64_t stream = l2_stream();
+  const int w = a.w;
+  vsi = __ldg(a.vs + row);
+  if constexpr (FIRST) {
+    own = ldg_row(static_cast<const TG*>(a.tg) + row * w + sub * 4);
+    sc = -__ldg(a.scale + row);
+  } else {
+    ivsi = __ldg(a.ivs + row);
+    prev = ld4h(static_cast<const TP*>(a.tp) + row * w + sub * 4, stream);
+    own = ldg_row(static_cast<const float*>(a.tg) + row * w + sub * 4);
+    if (a.psi != nullptr) p = ld4h(a.psi + row * a.ldp + sub * 4, stream);
+  }
+}
+
+// Rows [r, r + rows) of a staged chunk; dot partials into acc (lane 0 of each row's lead slot).
+template <int LPR, bool FIRST, typename TG, typename TP>
+__device__ __forceinline__ void process_chunk(const StepArgs& a, const StageChunk& st, int r, int rows,
+                                              float c0, float c1, double (&acc)[FIRST ? 3 : 2]) {
+  constexpr int S = 32 / LPR;
+  constexpr int kLines = LPR >= 8 ? LPR / 8 : 1;  // 128-byte lines per gathered row (float)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int slot = lane / LPR, sub = lane % LPR;
+  int spr = 1;
+  while (spr < S && spr * kEdgesPerSlot < st.maxdeg) spr <<= 1;
+  const int rpw = S / spr;
+  const int rpp = (kBlock / 32) * rpw;
+  const int q = slot % spr;
+  const int rw = slot / spr;
+  const TG* __restrict__ base = static_cast<const TG*>(a.tg) + sub * 4;
+  const int w = a.w;
+  const bool scaled = FIRST || a.val != nullptr;
+  for (int p0 = 0; p0 < rows; p0 += rpp) {
+    const int rl = p0 + wid * rpw + rw;
+    const bool valid = rl < rows;
+    const bool lead = valid && q == 0;
+    const int64_t row = (int64_t)r + (valid ? rl : 0);
+    float4 own = make_float4(0.f, 0.f, 0.f, 0.f), prev = own, p = own;
+    float sc = 0.f, vsi = 1.f, ivsi = 1.f;
+    if (lead) row_operands<FIRST, TG, TP>(a, row, sub, own, prev, p, sc, vsi, ivsi);
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      const int beg = st.rp[rl], end = st.rp[rl + 1];
+      for (int e0 = beg + q; e0 < end; e0 += kRowUnroll * spr) {
+        if (!FIRST && a.l2pf) {
+          // the next batch's rows into L2 while this batch loads (pays off when the gathered
+          // block exceeds the L2)
+          for (int qq = sub; qq < kRowUnroll * kLines; qq += LPR) {
+            const int ep = e0 + (kRowUnroll + qq / kLines) * spr;
+            if (ep < end)
+              asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(
+                  static_cast<const float*>(a.tg) + (int64_t)st.u.e.col[ep] * w + (qq % kLines) * 32)
+                           : "memory");
+          }
+        }
+        float4 v[kRowUnroll];
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u) {
+          const int e = e0 + u * spr;
+          v[u] = e < end ? ldg_row(base + (int64_t)st.u.e.col[e] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (scaled) {
+#pragma unroll
+          for (int u = 0; u < kRowUnroll; ++u)
+            if (e0 + u * spr < end) fma4(g, st.u.e.wt[e0 + u * spr], v[u]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < kRowUnroll; ++u) {
+            g.x += v[u].x; g.y += v[u].y; g.z += v[u].z; g.w += v[u].w;
+          }
+        }
+      }
+    }
+    for (int off = LPR; off < LPR * spr; off <<= 1) g = shfl_xor4(g, off);
+    float dots[3] = {0.f, 0.f, 0.f};
+    if (lead) row_epilogue<FIRST>(a, row, sub, g, own, prev, p, c0, c1, sc, vsi, ivsi, dots);
+#pragma unroll
+    for (int k = 0; k < (FIRST ? 3 : 2); ++k)
+#pragma unroll
+      for (int off = 1; off < LPR; off <<= 1) dots[k] += __shfl_xor_sync(kFull, dots[k], off);
+    if (lead && sub == 0) {
+      acc[0] += (double)dots[0];
+      acc[1] += (double)dots[1];
+      if constexpr (FIRST) acc[FIRST ? 2 : 0] += (double)dots[2];
+    }
+  }
+}
+
+// A row too long to stage, reduced by the whole CTA from global memory.
+template <int LPR, bool FIRST, typename TG, typename TP>
+__device__ __forceinline__ void coop_row(const StepArgs& a, StageChunk& st, int64_t row, float c0, float c1,
+                                         double (&acc)[FIRST ? 3 : 2]) {
+  constexpr int S = 32 / LPR;
+  constexpr int TS = (kBlock / 32) * S;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int slot = lane / LPR, sub = lane % LPR;
+  const int gs = wid * S + slot;
+  const bool lead = threadIdx.x < LPR;
+  float4 own = make_float4(0.f, 0.f, 0.f, 0.f), prev = own, p = own;
+  float sc = 0.f, vsi = 1.f, ivsi = 1.f;
+  if (lead) row_operands<FIRST, TG, TP>(a, row, sub, own, prev, p, sc, vsi, ivsi);
+  const TG* __restrict__ base = static_cast<const TG*>(a.tg) + sub * 4;
+  const int w = a.w;
+  const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
+  float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t e0 = beg + gs; e0 < end; e0 += (int64_t)kRowUnroll * TS) {
+    int c[kRowUnroll];
+    float wt[kRowUnroll];
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) {
+      const int64_t e = e0 + (int64_t)u * TS;
+      c[u] = e < end ? __ldcs(a.col + e) : 0;
+      wt[u] = e < end ? (a.val != nullptr ? __ldcs(a.val + e) : 1.0f) : 0.0f;
+    }
+    if (FIRST) {
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) wt[u] *= __ldg(a.scale + c[u]);
+    }
+    float4 v[kRowUnroll];
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u)
+      v[u] = e0 + (int64_t)u * TS < end ? ldg_row(base + (int64_t)c[u] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kRowUnroll; ++u) fma4(g, wt[u], v[u]);
+  }
+#pragma unroll
+  for (int off = LPR; off < 32; off <<= 1) g = shfl_xor4(g, off);
+  __syncthreads();  // the warp sums alias the previous chunk's staged edges
+  if (slot == 0) st.u.red[wid][sub] = g;
+  __syncthreads();
+  if (wid == 0) {
+    float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lead) {
+      for (int k = 0; k < kBlock / 32; ++k) {
+        const float4 h = st.u.red[k][sub];
+        tot.x += h.x; tot.y += h.y; tot.z += h.z; tot.w += h.w;
+      }
+    }
+    float dots[3] = {0.f, 0.f, 0.f};
+    if (lead) row_epilogue<FIRST>(a, row, sub, tot, own, prev, p, c0, c1, sc, vsi, ivsi, dots);
+#pragma unroll
+    for (int k = 0; k < (FIRST ? 3 : 2); ++k)
+#pragma unroll
+      for (int off = 1; off < LPR; off <<= 1) dots[k] += __shfl_xor_sync(kFull, dots[k], off);
+    if (threadIdx.x == 0) {
+      acc[0] += (double)dots[0];
+      acc[1] += (double)dots[1];
+      if constexpr (FIRST) acc[FIRST ? 2 : 0] += (double)dots[2];
+    }
+  }
+}
+
+// FIRST: T_1 = L~ T_0 (stored as V_1 = vs T_1), Psi = a_0 T_0 + a_1 T_1, partials <T0,T0>,
+// <T1,T1>, <T1,T0> (TG: storage type of T_0).  Else one general step (TP: storage type of
+// T_{j-1}), partials <T_{j+1},T_{j+1}>, <T_{j+1},T_j>.  Four CTAs per SM (at most 64 registers
+// per thread) keep more gathers in flight.
+template <int LPR, bool FIRST, typename TG, typename TP>
+__global__ void __launch_bounds__(kBlock, 4) cheb_rows_kernel(StepArgs a) {
+  constexpr int NQ = FIRST ? 3 : 2;
+  __shared__ StageChunk st;
+  double acc[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) acc[k] = 0.0;
+  float c0 = 0.f, c1 = 0.f;
+  if (a.psi != nullptr) {
+    if (FIRST) {
+      c0 = __ldg(a.coef);
+      c1 = __ldg(a.coef + 1);
+    } else {
+      c1 = __ldg(a.coef + a.j + 1);
+    }
+  }
+  for (int b = blockIdx.x; b < a.nsblk; b += gridDim.x) {
+    const int re = __ldg(a.srow + b + 1);
+    int r = __ldg(a.srow + b);
+    while (r < re) {
+      const int rows = stage_chunk<FIRST>(a, st, r, re);
+      if (rows == 0) {
+        coop_row<LPR, FIRST, TG, TP>(a, st, r, c0, c1, acc);
+        r += 1;
+      } else {
+        process_chunk<LPR, FIRST, TG, TP>(a, st, r, rows, c0, c1, acc);
+        r += rows;
+      }
+    }
+  }
   // every lane may hold a partial: reduce the warp first
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    acc[0] += __shfl_xor_sync(kFull, acc[0], off);
-    acc[1] += __shfl_xor_sync(kFull, acc[1], off);
-  }
-  block_store<2>(acc, a.part);
+  for (int k = 0; k < NQ; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(kFull, acc[k], off);
+  block_store<NQ>(acc, a.part);
 }
 
 // ------------------------------------------------------------------ batched filtering
@@ -681,26 +875,14 @@ __global__ void __launch_bounds__(kBlock, 3) cheb_batched_kernel(const BatchTile
   }
 }
 
-template <typename T0>
-const void* first_kernel_for(int lpr) {
+template <bool FIRST, typename TG, typename TP>
+const void* rows_kernel_for(int lpr) {
   switch (lpr) {
-    case 2: return (const void*)cheb_first_kernel<2, T0>;
-    case 4: return (const void*)cheb_first_kernel<4, T0>;
-    case 8: return (const void*)cheb_first_kernel<8, T0>;
-    case 16: return (const void*)cheb_first_kernel<16, T0>;
-    case 32: return (const void*)cheb_first_kernel<32, T0>;
-  }
-  return nullptr;
-}
-
-template <typename TP>
-const void* step_kernel_for(int lpr) {
-  switch (lpr) {
-    case 2: return (const void*)cheb_step_kernel<2, TP>;
-    case 4: return (const void*)cheb_step_kernel<4, TP>;
-    case 8: return (const void*)cheb_step_kernel<8, TP>;
-    case 16: return (const void*)cheb_step_kernel<16, TP>;
-    case 32: return (const void*)cheb_step_kernel<32, TP>;
+    case 2: return (const void*)cheb_rows_kernel<2, FIRST, TG, TP>;
+    case 4: return (const void*)cheb_rows_kernel<4, FIRST, TG, TP>;
+    case 8: return (const void*)cheb_rows_kernel<8, FIRST, TG, TP>;
+    case 16: return (const void*)cheb_rows_kernel<16, FIRST, TG, TP>;
+    case 32: return (const void*)cheb_rows_kernel<32, FIRST, TG, TP>;
   }
   return nullptr;
 }
@@ -738,36 +920,25 @@ int cheb_grid(int w) {
   static int grid = 0;
   if (grid == 0) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_step_kernel<4, float>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_rows_kernel<4, false, float, float>, kBlock, 0);
     if (per_sm < 1) per_sm = 1;
     grid = per_sm * num_sms();
   }
   return grid;
 }
 
-// Rows per block of the row-parallel kernels: whole passes of the row slots, at most kStepRows,
-// about two blocks per CTA of the grid on small graphs.
-int rows_per_block(int64_t n, int lpr, int grid) {
-  const int64_t rpp = (kBlock / 32) * (32 / lpr);
-  const int64_t want = (n + 2 * (int64_t)grid - 1) / (2 * (int64_t)grid);
-  return (int)std::min<int64_t>(kStepRows, std::max<int64_t>(rpp, (want + rpp - 1) / rpp * rpp));
-}
-
 cudaError_t launch_cheb_first(const StepArgs& a, int t0_dtype, int grid, cudaStream_t s) {
   const int lpr = a.w / 4;
-  const void* fn = t0_dtype == CSC_BF16 ? first_kernel_for<__nv_bfloat16>(lpr)
-                                        : first_kernel_for<float>(lpr);
-  StepArgs b = a;
-  b.rpb = rows_per_block(a.n, lpr, grid);
-  return launch_any(fn, b, grid, s);
+  const void* fn = t0_dtype == CSC_BF16 ? rows_kernel_for<true, __nv_bfloat16, float>(lpr)
+                                        : rows_kernel_for<true, float, float>(lpr);
+  return launch_any(fn, a, grid, s);
 }
 
 cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStream_t s) {
   const int lpr = a.w / 4;
-  const void* fn = tp_dtype == CSC_BF16 ? step_kernel_for<__nv_bfloat16>(lpr)
-                                        : step_kernel_for<float>(lpr);
+  const void* fn = tp_dtype == CSC_BF16 ? rows_kernel_for<false, float, __nv_bfloat16>(lpr)
+                                        : rows_kernel_for<false, float, float>(lpr);
   StepArgs b = a;
-  b.rpb = rows_per_block(a.n, lpr, grid);
   b.l2pf = (double)a.n * a.w * 4.0 > 64.0 * (1 << 20);
   return launch_any(fn, b, grid, s);
 }

@@ -249,6 +249,13 @@ __global__ void argmax_kernel(const float* __restrict__ x, int64_t ldx, int64_t 
 
 }  // namespace
 
+int64_t scan_sums_len(int64_t n) { return (n + kScanChunk - 1) / kScanChunk + 1; }
+
+cudaError_t inclusive_scan_i64(const long long* in, long long* out, int64_t n, long long* sums, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  return inclusive_scan<long long>(in, out, n, sums, s);
+}
+
 cudaError_t compressive_sample(CompressiveState& cs, const float* theta, int64_t ld, int64_t n, int d,
                                int64_t n_draws, uint64_t seed, cudaStream_t s) {
   const int64_t nb = (n + kScanChunk - 1) / kScanChunk;

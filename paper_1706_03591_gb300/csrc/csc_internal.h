@@ -41,9 +41,26 @@ struct Graph {
   DevBuf vs;        // float[n], row scale of the value-free recursion: D^{-1/2}, 1 if isolated
   DevBuf ivs;       // float[n], 1 / vs
   DevBuf deg;       // double[n]
-  DevBuf blk_row;   // int32[nblk+1], edge-block partition of the rows for the recursion
+  DevBuf blk_row;   // int32[nblk+1], edge-block partition of the rows (batched kernel)
+  DevBuf srow;      // int32[nsblk+1], weight-balanced row blocks of the step kernels
   bool loaded = false;
+  // Internal node order (csc_opts.reorder): internal row i holds caller row perm[i] (degrees
+  // descending, ties by caller id), its neighbours in the caller's order with the ids mapped
+  // through iperm; the caller's CSR stays on the device beside it.
+  bool permuted = false;
+  DevBuf perm;      // int32[n]: internal row -> caller row
+  DevBuf iperm;     // int32[n]: caller row -> internal row
+  DevBuf urp;       // int64[n+1]: caller row offsets
+  DevBuf ucol;      // int32[nnz]: caller column indices
+  DevBuf uval;      // float[nnz]: caller edge weights (weighted graphs)
+  std::vector<int32_t> h_perm, h_iperm;
 };
+
+// Row blocks of the step kernels: a row weighs its stored edges plus kRowCost (its own
+// streams), and block b starts at the first row whose cumulative weight reaches b * kBlockWeight.
+constexpr int kRowCost = 4;
+constexpr int kBlockWeight = 4096;
+int row_blocks(int64_t n, int64_t nnz);
 
 // Target number of stored edges per block of the recursion kernels (staged in shared memory).
 constexpr int kEdgesPerBlock = 2048;
@@ -65,7 +82,15 @@ void filter_coeffs(int m, double lambda_c, double* a);
 // ------------------------------------------------------------------ graph kernels (graph.cu)
 
 cudaError_t launch_graph_prep(const Graph& g, cudaStream_t s);
-// Computes g.blk_row (edge_blocks(g.nnz) + 1 entries).
+// Internal CSR of g from its caller CSR (urp/ucol/uval) and perm/iperm (g.deg is used as
+// scratch); deg_tmp: int64[n] scratch, sums: scan_sums_len(n) int64 scratch.
+cudaError_t launch_permute_graph(Graph& g, long long* deg_tmp, long long* sums, cudaStream_t s);
+// dst[i] = src[map[i]] for i < n (int32 vectors).
+cudaError_t launch_gather_i32(int32_t* dst, const int32_t* src, const int32_t* map, int64_t n, cudaStream_t s);
+// Edge values of the internal CSR scattered to the caller's edge order: dst[urp[perm[i]] + k] =
+// src[row_ptr[i] + k].
+cudaError_t launch_scatter_edges(const Graph& g, const float* src, float* dst, cudaStream_t s);
+// Computes g.blk_row (edge_blocks(g.nnz) + 1 entries) and g.srow (row_blocks(g.n, g.nnz) + 1).
 cudaError_t launch_block_rows(const Graph& g, cudaStream_t s);
 // Device-side CSR validation; writes the number of violations into *bad (device int64).
 cudaError_t launch_graph_check(const Graph& g, unsigned long long* bad, cudaStream_t s);
@@ -74,12 +99,16 @@ cudaError_t launch_graph_check(const Graph& g, unsigned long long* bad, cudaStre
 
 // Fills an n x w block (leading dimension w) of tile columns [col0, col0 + valid) of the
 // Philox N(0, 1/d) signals; columns >= valid are zero.  dtype CSC_F32 / CSC_BF16.
+// rowid (nullptr: identity): the Philox row counter of output row i is rowid[i].
 cudaError_t launch_signals(void* out, int dtype, int64_t n, int w, int64_t ld, uint64_t seed,
-                           int64_t col0, int valid, float inv_sqrt_d, cudaStream_t s);
+                           int64_t col0, int valid, float inv_sqrt_d, cudaStream_t s,
+                           const int32_t* rowid = nullptr);
 // Copies columns [c0, c0 + valid) of a caller block (n x ld_src, dtype) into an n x w
-// tile buffer of the same dtype, zero-filling columns >= valid.
+// tile buffer of the same dtype, zero-filling columns >= valid; row i of the tile is row
+// src_row[i] of the caller block (nullptr: row i).
 cudaError_t launch_copy_tile(void* dst, const void* src, int dtype, int64_t n, int w,
-                             int64_t ld_src, int c0, int valid, cudaStream_t s);
+                             int64_t ld_src, int c0, int valid, cudaStream_t s,
+                             const int32_t* src_row = nullptr);
 
 // ------------------------------------------------------------------ Chebyshev recursion (cheb.cu)
 
@@ -93,7 +122,8 @@ struct StepArgs {
   const float* ivs;     // 1 / vs
   const int32_t* blk_row;  // edge-block partition (nblk + 1)
   int nblk;
-  int rpb;              // rows per block of the general step (set by launch_cheb_step)
+  const int32_t* srow;  // weight-balanced row blocks of the step kernels (nsblk + 1)
+  int nsblk;
   int l2pf;             // prefetch the next batch of gathered rows into L2 (set by launch_cheb_step)
   int tp_unscaled;      // 1: tp holds T_{j-1} (step 2 reads T_0 = R), 0: tp holds V_{j-1}
   const void* tg;       // gathered block T_j (n x w)
@@ -153,8 +183,10 @@ cudaError_t launch_assemble(float* theta, int64_t ldt, const float* psi, int64_t
                             const int* src, int d, void* y, int y_dtype, int64_t ldy, int64_t n,
                             cudaStream_t s);
 // Copies an n x d block (src dtype float or bf16, ld_src) to dst (dtype, ld_dst) on device.
+// Row i of dst is row src_row[i] of src (nullptr: row i).
 cudaError_t launch_convert(const void* src, int src_dtype, int64_t ld_src, void* dst,
-                           int dst_dtype, int64_t ld_dst, int64_t n, int d, cudaStream_t s);
+                           int dst_dtype, int64_t ld_dst, int64_t n, int d, cudaStream_t s,
+                           const int32_t* src_row = nullptr);
 
 // ------------------------------------------------------------------ differentiation (grad.cu)
 
@@ -178,6 +210,7 @@ struct GradState {
   DevBuf part;                // double block partials of <dloss/dPsi, T_j>
   DevBuf ga;                  // double [m + 1][ntiles]: per-tile <dloss/dPsi, T_j R>
   DevBuf flag;                // int64: entries without a transposed partner
+  DevBuf gw_stage;            // float [nnz]: edge gradients in the internal edge order
   int64_t graph_version = -1; // graph the transpose map was built for
 };
 
@@ -208,6 +241,8 @@ cudaError_t compressive_gather(const void* y, int y_dtype, int64_t ldy, const in
 cudaError_t compressive_rhs(const CompressiveState& cs, const int32_t* labels, int64_t no, int64_t n, float* z,
                             int64_t ldz, cudaStream_t s);
 // out[i] = lowest index of the maximum of row i of x (k columns).
+int64_t scan_sums_len(int64_t n);
+cudaError_t inclusive_scan_i64(const long long* in, long long* out, int64_t n, long long* sums, cudaStream_t s);
 cudaError_t compressive_argmax(const float* x, int64_t ldx, int64_t n, int k, int32_t* out, cudaStream_t s);
 void compressive_release(CompressiveState& cs);
 
@@ -314,6 +349,7 @@ struct csc_ctx {
   csc::DevBuf astage;      // caller assignment staged on the device
   csc::DevBuf out_stage;   // conversions before a host copy
   csc::DevBuf bad;         // CSR violation counter
+  csc::DevBuf gtmp;        // set_graph scratch: int64 [n] + scan sums
   // counters (csc_get_stats)
   int64_t launches = 0, step_launches = 0, filter_passes = 0;
   double step_ms = 0.0;

@@ -65,13 +65,14 @@ __global__ void assemble_kernel(float* __restrict__ theta, int64_t ldt, const fl
 
 template <typename TS, typename TD>
 __global__ void convert_kernel(const TS* __restrict__ src, int64_t ld_src, TD* __restrict__ dst,
-                               int64_t ld_dst, int64_t n, int d) {
+                               int64_t ld_dst, int64_t n, int d, const int32_t* __restrict__ src_row) {
   const int64_t total = n * (int64_t)d;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = e / d;
     const int q = (int)(e - row * d);
-    put<TD>(dst + row * ld_dst + q, get(src + row * ld_src + q));
+    const int64_t r = src_row != nullptr ? (int64_t)src_row[row] : row;
+    put<TD>(dst + row * ld_dst + q, get(src + r * ld_src + q));
   }
 }
 
@@ -109,23 +110,24 @@ cudaError_t launch_assemble(float* theta, int64_t ldt, const float* psi, int64_t
 }
 
 cudaError_t launch_convert(const void* src, int src_dtype, int64_t ld_src, void* dst,
-                           int dst_dtype, int64_t ld_dst, int64_t n, int d, cudaStream_t s) {
+                           int dst_dtype, int64_t ld_dst, int64_t n, int d, cudaStream_t s,
+                           const int32_t* src_row) {
   if (n == 0 || d == 0) return cudaSuccess;
   const int grid = grid_rows(n * (int64_t)d, 256);
   if (src_dtype == CSC_BF16) {
     if (dst_dtype == CSC_BF16)
       convert_kernel<__nv_bfloat16, __nv_bfloat16><<<grid, 256, 0, s>>>(
-          (const __nv_bfloat16*)src, ld_src, (__nv_bfloat16*)dst, ld_dst, n, d);
+          (const __nv_bfloat16*)src, ld_src, (__nv_bfloat16*)dst, ld_dst, n, d, src_row);
     else
       convert_kernel<__nv_bfloat16, float><<<grid, 256, 0, s>>>((const __nv_bfloat16*)src, ld_src,
-                                                                (float*)dst, ld_dst, n, d);
+                                                                (float*)dst, ld_dst, n, d, src_row);
   } else {
     if (dst_dtype == CSC_BF16)
       convert_kernel<float, __nv_bfloat16><<<grid, 256, 0, s>>>((const float*)src, ld_src,
-                                                                (__nv_bfloat16*)dst, ld_dst, n, d);
+                                                                (__nv_bfloat16*)dst, ld_dst, n, d, src_row);
     else
       convert_kernel<float, float><<<grid, 256, 0, s>>>((const float*)src, ld_src, (float*)dst,
-                                                        ld_dst, n, d);
+                                                        ld_dst, n, d, src_row);
   }
   return cudaGetLastError();
 }

@@ -214,6 +214,35 @@ __global__ void transpose_index_kernel(int64_t n, const int64_t* __restrict__ ro
   }
 }
 
+// The same for an internally reordered graph whose rows keep the caller's neighbour order:
+// internal edge (i, offset k) is caller edge urp[perm[i]] + k; its transpose is found by binary
+// search in the caller's sorted row and mapped back by its offset.
+__global__ void transpose_index_perm_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
+                                            const int64_t* __restrict__ urp, const int32_t* __restrict__ ucol,
+                                            const int32_t* __restrict__ perm, const int32_t* __restrict__ iperm,
+                                            int32_t* __restrict__ tpos, unsigned long long* bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    const int64_t beg = row_ptr[i], end = row_ptr[i + 1];
+    const int32_t u = perm[i];
+    const int64_t ub = urp[u];
+    for (int64_t e = beg + lane; e < end; e += 32) {
+      const int v = ucol[ub + (e - beg)];
+      int64_t lo = urp[v], hi = urp[v + 1];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ucol[mid] < u) lo = mid + 1;
+        else hi = mid;
+      }
+      const bool found = lo < urp[v + 1] && ucol[lo] == u;
+      tpos[e] = found ? (int32_t)(row_ptr[iperm[v]] + (lo - urp[v])) : -1;
+      if (!found) atomicAdd(bad, 1ull);
+    }
+  }
+}
+
 // s_u = -sum_{b in row u} w_ub (H_ub + H_bu): one warp per row.
 __global__ void weight_node_sum_kernel(int64_t n, const int64_t* __restrict__ row_ptr, const float* __restrict__ val,
                                        const float* __restrict__ H, const int32_t* __restrict__ tpos,
@@ -339,6 +368,10 @@ cudaError_t launch_adjoint(const AdjArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Row maps between the caller's node order and the internal one (nullptr: the same order).
+const int32_t* to_caller(csc_ctx* ctx) { return ctx->g.permuted ? as<int32_t>(ctx->g.perm) : nullptr; }
+const int32_t* to_internal(csc_ctx* ctx) { return ctx->g.permuted ? as<int32_t>(ctx->g.iperm) : nullptr; }
+
 StepArgs step_args(csc_ctx* ctx, int w, double* part) {
   StepArgs sa{};
   sa.n = ctx->g.n;
@@ -350,6 +383,8 @@ StepArgs step_args(csc_ctx* ctx, int w, double* part) {
   sa.ivs = as<float>(ctx->g.ivs);
   sa.blk_row = as<int32_t>(ctx->g.blk_row);
   sa.nblk = edge_blocks(ctx->g.nnz);
+  sa.srow = as<int32_t>(ctx->g.srow);
+  sa.nsblk = row_blocks(ctx->g.n, ctx->g.nnz);
   sa.coef = as<float>(ctx->gs.coef_f);
   sa.w = w;
   sa.part = part;
@@ -435,7 +470,7 @@ extern "C" csc_status csc_filter_forward(csc_ctx* ctx, int m, const double* coef
   float* psi_tile = csc::as<float>(gs.gt);
   for (int tile = 0; tile < gs.ntiles; ++tile) {
     const int c0 = tile * w, valid = std::min(w, c - c0);
-    G_CUDA(csc::launch_copy_tile(gs.rt.ptr, R, CSC_F32, n, w, ldr, c0, valid, s));
+    G_CUDA(csc::launch_copy_tile(gs.rt.ptr, R, CSC_F32, n, w, ldr, c0, valid, s, csc::to_caller(ctx)));
     G_CUDA(cudaMemsetAsync(psi_tile, 0, blk * 4, s));
     float* tile_ck = ck + (size_t)tile * gs.slots * blk;
     auto vp = [&](int j) { return csc::as<float>(ctx->tbuf[j % 3]); };  // V_j lives in tbuf[j % 3]
@@ -450,8 +485,7 @@ extern "C" csc_status csc_filter_forward(csc_ctx* ctx, int m, const double* coef
       if (slot >= 0)
         G_CUDA(cudaMemcpyAsync(tile_ck + (size_t)slot * blk, vp(v), blk * 4, cudaMemcpyDeviceToDevice, s));
     }
-    G_CUDA(cudaMemcpy2DAsync(psi_out + c0, (size_t)ldp * 4, psi_tile, (size_t)w * 4, (size_t)valid * 4, n,
-                             cudaMemcpyDeviceToDevice, s));
+    G_CUDA(csc::launch_convert(psi_tile, CSC_F32, w, psi_out + c0, CSC_F32, ldp, n, valid, s, csc::to_internal(ctx)));
   }
   gs.ready = true;
   return CSC_OK;
@@ -485,8 +519,8 @@ extern "C" csc_status csc_filter_vjp(csc_ctx* ctx, const float* grad_psi, int64_
   const float* ck = csc::as<float>(gs.ckpt);
   for (int tile = 0; tile < gs.ntiles; ++tile) {
     const int c0 = tile * w, valid = std::min(w, gs.c - c0);
-    G_CUDA(csc::launch_copy_tile(gs.rt.ptr, gs.R, CSC_F32, n, w, gs.ldr, c0, valid, s));
-    G_CUDA(csc::launch_copy_tile(gs.gt.ptr, grad_psi, CSC_F32, n, w, ldg, c0, valid, s));
+    G_CUDA(csc::launch_copy_tile(gs.rt.ptr, gs.R, CSC_F32, n, w, gs.ldr, c0, valid, s, csc::to_caller(ctx)));
+    G_CUDA(csc::launch_copy_tile(gs.gt.ptr, grad_psi, CSC_F32, n, w, ldg, c0, valid, s, csc::to_caller(ctx)));
     const float* tile_ck = ck + (size_t)tile * gs.slots * blk;
     // V_j of the current segment [lo, hi]: seg slot j - lo + 1 (slot 0 holds V_{lo-1})
     int lo = 0, hi = 0;
@@ -552,10 +586,16 @@ extern "C" csc_status csc_filter_vjp(csc_ctx* ctx, const float* grad_psi, int64_
       G_ALLOC(csc::ensure(gs.tpos, (size_t)nnz * 4));
       G_ALLOC(csc::ensure(gs.flag, 8));
       G_CUDA(cudaMemsetAsync(gs.flag.ptr, 0, 8, s));
-      csc::transpose_index_kernel<<<sms * 8, csc::kBlk, 0, s>>>(n, csc::as<int64_t>(ctx->g.row_ptr),
-                                                                csc::as<int32_t>(ctx->g.col),
-                                                                csc::as<int32_t>(gs.tpos),
-                                                                csc::as<unsigned long long>(gs.flag));
+      if (ctx->g.permuted)
+        csc::transpose_index_perm_kernel<<<sms * 8, csc::kBlk, 0, s>>>(
+            n, csc::as<int64_t>(ctx->g.row_ptr), csc::as<int64_t>(ctx->g.urp), csc::as<int32_t>(ctx->g.ucol),
+            csc::as<int32_t>(ctx->g.perm), csc::as<int32_t>(ctx->g.iperm), csc::as<int32_t>(gs.tpos),
+            csc::as<unsigned long long>(gs.flag));
+      else
+        csc::transpose_index_kernel<<<sms * 8, csc::kBlk, 0, s>>>(n, csc::as<int64_t>(ctx->g.row_ptr),
+                                                                  csc::as<int32_t>(ctx->g.col),
+                                                                  csc::as<int32_t>(gs.tpos),
+                                                                  csc::as<unsigned long long>(gs.flag));
       G_CUDA(cudaGetLastError());
       unsigned long long bad = 0;
       G_CUDA(cudaMemcpyAsync(&bad, gs.flag.ptr, 8, cudaMemcpyDeviceToHost, s));
@@ -570,12 +610,22 @@ extern "C" csc_status csc_filter_vjp(csc_ctx* ctx, const float* grad_psi, int64_
                                                               csc::as<float>(gs.H), csc::as<int32_t>(gs.tpos),
                                                               csc::as<double>(gs.nsum));
     G_CUDA(cudaGetLastError());
+    // per internal edge; scattered to the caller's edge order when the graph is reordered
+    float* gw = grad_w;
+    if (ctx->g.permuted) {
+      G_ALLOC(csc::ensure(gs.gw_stage, (size_t)nnz * 4));
+      gw = csc::as<float>(gs.gw_stage);
+    }
     csc::weight_grad_kernel<<<sms * 8, csc::kBlk, 0, s>>>(n, csc::as<int64_t>(ctx->g.row_ptr),
                                                           csc::as<int32_t>(ctx->g.col), csc::as<float>(gs.H),
                                                           csc::as<int32_t>(gs.tpos), csc::as<double>(gs.nsum),
-                                                          csc::as<double>(ctx->g.deg), grad_w);
+                                                          csc::as<double>(ctx->g.deg), gw);
     G_CUDA(cudaGetLastError());
     ctx->launches += 2;
+    if (ctx->g.permuted) {
+      G_CUDA(csc::launch_scatter_edges(ctx->g, gw, grad_w, s));
+      ctx->launches += 1;
+    }
   }
   G_CUDA(cudaStreamSynchronize(s));
   if (grad_coef != nullptr)

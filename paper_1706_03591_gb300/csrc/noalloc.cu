@@ -41,7 +41,9 @@ constexpr size_t kOffVs = kOffScale + align256(kMaxN * 4);
 constexpr size_t kOffIvs = kOffVs + align256(kMaxN * 4);
 constexpr size_t kOffDeg = kOffIvs + align256(kMaxN * 4);
 constexpr size_t kOffBlk = kOffDeg + align256(kMaxN * 8);
-constexpr size_t kOffT = kOffBlk + align256((kMaxNnz / csc::kEdgesPerBlock + 2) * 4);
+constexpr size_t kOffSrow = kOffBlk + align256((kMaxNnz / csc::kEdgesPerBlock + 2) * 4);
+constexpr size_t kOffT =
+    kOffSrow + align256(((kMaxNnz + csc::kRowCost * kMaxN) / csc::kBlockWeight + 2) * 4);
 constexpr size_t kOffPsi = kOffT + 3 * align256(kMaxN * kTile * 4);
 constexpr size_t kOffCoef = kOffPsi + align256(kMaxN * kTile * 4);
 constexpr size_t kOffPart = kOffCoef + align256((kMaxM + 1) * 4);
@@ -114,6 +116,7 @@ extern "C" csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int6
   g.ivs.ptr = base + kOffIvs;
   g.deg.ptr = base + kOffDeg;
   g.blk_row.ptr = base + kOffBlk;
+  g.srow.ptr = base + kOffSrow;
   NA_CHECK(csc::launch_graph_prep(g, s));
   NA_CHECK(csc::launch_block_rows(g, s));
   float* tb[3] = {reinterpret_cast<float*>(base + kOffT),
@@ -148,6 +151,8 @@ extern "C" csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int6
     sa.ivs = static_cast<const float*>(g.ivs.ptr);
     sa.blk_row = static_cast<const int32_t*>(g.blk_row.ptr);
     sa.nblk = csc::edge_blocks(nnz);
+    sa.srow = static_cast<const int32_t*>(g.srow.ptr);
+    sa.nsblk = csc::row_blocks(n, nnz);
     sa.psi = psi;
     sa.ldp = kTile;
     sa.coef = coef;

@@ -46,8 +46,8 @@ def small_case(c, seed=7):
     return g, w, r, a, mu, assign
 
 
-def gpu_grads(gpu_lib, g, w, r, a, mu, assign, stride):
-    with gpu_lib.Context() as ctx:
+def gpu_grads(gpu_lib, g, w, r, a, mu, assign, stride, reorder=1):
+    with gpu_lib.Context({"reorder": reorder}) as ctx:
         ctx.set_graph(g.n, torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(),
                       None if w is None else torch.from_numpy(w).cuda())
         rt = torch.from_numpy(r).cuda()
@@ -60,10 +60,10 @@ def gpu_grads(gpu_lib, g, w, r, a, mu, assign, stride):
         return psi.cpu().numpy(), loss, gpsi.cpu().numpy(), ga, gw.cpu().numpy()
 
 
-@pytest.mark.parametrize("c,stride", [(16, 0), (16, 1), (130, 7)])
-def test_gradients_match_oracle_and_finite_differences(gpu_lib, c, stride):
+@pytest.mark.parametrize("c,stride,reorder", [(16, 0, 1), (16, 1, 1), (130, 7, 1), (16, 0, 0)])
+def test_gradients_match_oracle_and_finite_differences(gpu_lib, c, stride, reorder):
     g, w, r, a, mu, assign = small_case(c)
-    psi, loss, gpsi, ga, gw = gpu_grads(gpu_lib, g, w, r, a, mu, assign, stride)
+    psi, loss, gpsi, ga, gw = gpu_grads(gpu_lib, g, w, r, a, mu, assign, stride, reorder)
     lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx, w)
     psi_ref = gr.filter_psi(lt, r, a)
     assert rel(psi, psi_ref) < 1e-5
@@ -75,7 +75,7 @@ def test_gradients_match_oracle_and_finite_differences(gpu_lib, c, stride):
     assert rel(ga, ga_ref) < 1e-4
     assert rel(gw, gw_ref) < 1e-4
     # central differences of the float64 loss on 64 random coordinates (coefficients and edges)
-    rng = np.random.default_rng(c + stride)
+    rng = np.random.default_rng(c + stride + 100 * reorder)
     rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
     w64 = w.astype(np.float64)
 

@@ -64,14 +64,15 @@ def test_signals_match_oracle_generator(gpu_lib):
         assert np.all(outb[:, c:].float().cpu().numpy() == 0)
 
 
+@pytest.mark.parametrize("reorder", [1, 0])
 @pytest.mark.parametrize("tile", [8, 16, 32, 64, 128])
 @pytest.mark.parametrize("c", [64, 13, 1])
-def test_cheb_filter_parity_tiles(gpu_lib, cfg1_graph, tile, c):
+def test_cheb_filter_parity_tiles(gpu_lib, cfg1_graph, tile, c, reorder):
     g = cfg1_graph
     lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
     r = W.gaussian_block(g.n, c, 64, seed=c * 7 + tile)
     m, lam = 50, 0.53
-    with gpu_lib.Context({"col_tile": tile}) as ctx:
+    with gpu_lib.Context({"col_tile": tile, "reorder": reorder}) as ctx:
         upload_graph(ctx, g)
         psi = torch.zeros((g.n, c), dtype=torch.float32, device="cuda")
         mu = ctx.cheb_filter(m, lam, dev(r), psi)
@@ -95,7 +96,8 @@ def test_cheb_filter_orders(gpu_lib, cfg1_graph, m):
     assert np.max(np.abs(mu - mu_ref)) < FP32_TOL * mu_ref[0]
 
 
-def test_cheb_filter_weighted_and_isolated(gpu_lib):
+@pytest.mark.parametrize("reorder", [1, 0])
+def test_cheb_filter_weighted_and_isolated(gpu_lib, reorder):
     g = W.random_csr(3001, 9, seed=4, isolated=40)
     rng = np.random.default_rng(0)
     upper_w = rng.uniform(0.1, 3.0, g.nnz)
@@ -106,7 +108,7 @@ def test_cheb_filter_weighted_and_isolated(gpu_lib):
     vals = upper_w[inv].astype(np.float32)
     lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx, vals)
     r = W.gaussian_block(g.n, 20, 32, seed=2)
-    with gpu_lib.Context({"col_tile": 16}) as ctx:
+    with gpu_lib.Context({"col_tile": 16, "reorder": reorder}) as ctx:
         upload_graph(ctx, g, vals)
         psi = torch.zeros((g.n, 20), device="cuda")
         ctx.cheb_filter(40, 0.8, dev(r), psi)
@@ -133,19 +135,42 @@ def _hub_graph(n=20000, deg=10, hubs=3, hub_degree=7000, seed=8):
     return n, np.cumsum(row_ptr), cols.astype(np.int32)
 
 
+@pytest.mark.parametrize("reorder", [1, 0])
 @pytest.mark.parametrize("tile", [8, 32, 64])
-def test_cheb_filter_hub_rows_beyond_the_staging_buffer(gpu_lib, tile):
+def test_cheb_filter_hub_rows_beyond_the_staging_buffer(gpu_lib, tile, reorder):
     n, rp, ci = _hub_graph()
     assert np.diff(rp).max() > 5632  # one hub row alone exceeds the staged edge buffer
     lt = lp.shifted_laplacian(n, rp, ci)
     r = W.gaussian_block(n, 40, 64, seed=9)
-    with gpu_lib.Context({"col_tile": tile}) as ctx:
+    with gpu_lib.Context({"col_tile": tile, "reorder": reorder}) as ctx:
         ctx.set_graph(n, dev(rp), dev(ci))
         psi = torch.zeros((n, 40), device="cuda")
         mu = ctx.cheb_filter(50, 0.7, dev(r), psi)
     ref = cb.cheb_filter(lt, r.astype(np.float64), 50, 0.7)
     assert rel(psi.cpu().numpy(), ref) < FP32_TOL
     mu_ref = cb.moments(lt, r.astype(np.float64), 100)
+    assert np.max(np.abs(mu - mu_ref)) < FP32_TOL * mu_ref[0]
+
+
+@pytest.mark.parametrize("reorder", [1, 0])
+@pytest.mark.parametrize("tile", [8, 32])
+def test_cheb_filter_power_law_graph(gpu_lib, tile, reorder):
+    """Chung-Lu graph with power-law degrees (exponent 2.5) and planted communities, the graph
+    class of the large workload: rows from degree 0 to about a thousand in one graph, so chunks
+    run from one slot per row to a whole warp per row (rows too long to stage are the hub
+    test's)."""
+    g = W.chung_lu_graph_torch(60000, 2.5, 25.0, 16, 0.2, seed=12).to_numpy()
+    deg = np.diff(g.row_ptr)
+    assert deg.max() > 512 and (deg == 0).any()
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    r = W.gaussian_block(g.n, 24, 64, seed=3)
+    with gpu_lib.Context({"col_tile": tile, "reorder": reorder}) as ctx:
+        upload_graph(ctx, g)
+        psi = torch.zeros((g.n, 24), device="cuda")
+        mu = ctx.cheb_filter(40, 0.3, dev(r), psi)
+    ref = cb.cheb_filter(lt, r.astype(np.float64), 40, 0.3)
+    assert rel(psi.cpu().numpy(), ref) < FP32_TOL
+    mu_ref = cb.moments(lt, r.astype(np.float64), 80)
     assert np.max(np.abs(mu - mu_ref)) < FP32_TOL * mu_ref[0]
 
 
@@ -320,14 +345,15 @@ def test_kmeans_exact_ties_lowest_index(gpu_lib):
     np.testing.assert_array_equal(out["assign"], lab_ref)
 
 
-def test_algorithm1_dynamic_parity_cfg1(gpu_lib, cfg1_graph):
+@pytest.mark.parametrize("reorder", [1, 0])
+def test_algorithm1_dynamic_parity_cfg1(gpu_lib, cfg1_graph, reorder):
     """SBM n=2000, k=10, degree 20, d=64, m=50, 1% rewiring per step, p=0.5: 1 + 5 snapshots."""
     n, k, d, m, p, seed = 2000, 10, 64, 50, 0.5, 2024
     graphs = [cfg1_graph]
     for t in range(5):
         graphs.append(W.edge_redraw(graphs[-1], 0.01, seed=100 + t))
     oracle = DynamicCSC(n, k, d, p, m, seed)
-    with gpu_lib.Context() as ctx:
+    with gpu_lib.Context({"reorder": reorder}) as ctx:
         assign = torch.zeros(n, dtype=torch.int32, device="cuda")
         for t, g in enumerate(graphs):
             idx = W.forgy_indices(n, k, seed=500 + t)

@@ -2,8 +2,9 @@
 GPU, host collectives over gloo.  Their kernels never wait on each other; only the host
 collectives between the filtering passes cross ranks.  Every rank must end each snapshot with the
 cutoff, dichotomy count, features and assignment of one process running csc_filter and
-csc_cluster on all columns (Algorithm 1, Eq. 6): each column's recursion is the same arithmetic
-whatever the tile it runs in, so the features match bit for bit."""
+csc_cluster on all columns (Algorithm 1, Eq. 6).  A rank filters fewer columns in narrower tiles,
+and a row's gather is split over a number of slots that depends on the tile width, so the
+features agree to float32 rounding rather than bit for bit."""
 import os
 import socket
 
@@ -83,5 +84,6 @@ def test_two_ranks_equal_single_context(gpu_lib, precision, p):
     for r in range(2):
         for t, ((lam, ev, assign, theta), (lam_r, ev_r, assign_r, theta_r)) in enumerate(zip(res[r], ref)):
             assert lam == lam_r and ev == ev_r, (r, t)
-            np.testing.assert_array_equal(theta, theta_r)
+            err = np.linalg.norm(theta - theta_r) / np.linalg.norm(theta_r)
+            assert err < 1e-6, (r, t, err)
             np.testing.assert_array_equal(assign, assign_r)

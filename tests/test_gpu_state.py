@@ -27,21 +27,21 @@ def _snapshot(ctx, g, t, n, k, d, m, p, seed):
     return lam, cnt, assign, theta
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_resume_continues_the_sequence_exactly(gpu_lib, tmp_path, precision):
+@pytest.mark.parametrize("precision,reorder", [(0, 1), (1, 1), (0, 0)])
+def test_resume_continues_the_sequence_exactly(gpu_lib, tmp_path, precision, reorder):
     n, k, d, m, p, seed = 2000, 10, 64, 50, 0.5, 11
     g0 = W.sbm_graph(n, k, 20, 10, seed=1)
     graphs = [g0]
     for t in range(1, 4):
         graphs.append(W.edge_redraw(graphs[-1], 0.01, seed=100 + t))
     path = tmp_path / "state.bin"
-    with gpu_lib.Context({"precision": precision}) as a:
+    with gpu_lib.Context({"precision": precision, "reorder": reorder}) as a:
         for t in range(2):
             _snapshot(a, graphs[t], t, n, k, d, m, p, seed)
         a.save_state(path)
         ref = [_snapshot(a, graphs[t], t, n, k, d, m, p, seed) for t in (2, 3)]
         mu_ref = gpu_lib.csc_get_moments(a.h, 2 * m + 1)
-    with gpu_lib.Context({"precision": precision}) as b:
+    with gpu_lib.Context({"precision": precision, "reorder": reorder}) as b:
         b.load_state(path)
         got = [_snapshot(b, graphs[t], t, n, k, d, m, p, seed) for t in (2, 3)]
         mu_got = gpu_lib.csc_get_moments(b.h, 2 * m + 1)
@@ -82,4 +82,7 @@ def test_state_errors(gpu_lib, tmp_path):
         ctx.filter(m, d, 0.5, 5, k)                      # the resumed context keeps working
     with gpu_lib.Context({"precision": 1}) as ctx:
         with pytest.raises(gpu_lib.CscError, match="precision"):
+            ctx.load_state(path)
+    with gpu_lib.Context({"reorder": 0}) as ctx:
+        with pytest.raises(gpu_lib.CscError, match="reorder"):
             ctx.load_state(path)
