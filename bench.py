@@ -209,13 +209,6 @@ def ncu_traffic(workload, tile):
     return None
 
 
-def step_bytes(n, nnz, tile):
-    """Algorithmic bytes of one Chebyshev step launch over one column tile (forward form):
-    col_idx 4 nnz + row_ptr 8(n+1) + D^-1/2 4n + T_{j-1}, T_j, T_{j+1} 3*4*n*w + Psi
-    read+write 2*4*n*w."""
-    return 4 * nnz + 8 * (n + 1) + 4 * n + 5 * 4 * n * tile
-
-
 def _oracle_columns(lt, n, d, cols, order, threads, seed):
     """Runs the float64 oracle filter on `cols` independent signal columns over the shared CSR
     `lt`, one column per thread (scipy's sparse products release the GIL); returns seconds."""
@@ -510,14 +503,18 @@ def run_sequence(ctx, cfg, n, graphs, nnz, seed, inits, assign, timed_from, cloc
 
 
 def roofline(stats, n, nnz_mean, tile, workload):
+    """The step kernel's algorithmic bytes (summed by the library over the timed launches, each
+    counted for its own tile width) over its CUDA-event time."""
     peak, peak_kind = peak_hbm()
-    avg_launch_s = stats["step_ms"] / max(1, stats["step_launches"]) / 1e3
-    bytes_launch = step_bytes(n, nnz_mean, tile)
-    achieved = bytes_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None
-    return {"kernel": "cheb_step", "bound": "hbm", "achieved": achieved, "peak": peak,
+    launches = max(1, stats["step_launches"])
+    avg_launch_s = stats["step_ms"] / launches / 1e3
+    bytes_launch = stats["step_bytes"] / launches
+    achieved = stats["step_bytes"] / (stats["step_ms"] / 1e3) / 1e9 if stats["step_ms"] > 0 else None
+    return {"kernel": "cheb_rows_kernel (general step)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if achieved else None,
             "traffic": ncu_traffic(workload, tile), "avg_launch_us": avg_launch_s * 1e6,
-            "launches_timed": stats["step_launches"], "bytes_per_launch": bytes_launch}
+            "launches_timed": stats["step_launches"], "bytes_per_launch": bytes_launch,
+            "widest_tile": tile}
 
 
 def sbm_extra(a, rank, dist, clocks_cls, local):

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 5
+#define CSC_ABI_VERSION 6
 
 typedef struct csc_ctx csc_ctx;
 
@@ -66,8 +66,9 @@ typedef struct csc_opts {
                        max(0.5, 2 sqrt(2k/c)) for a block of c signals */
   int max_bisect;   /* cap on eigencount evaluations of the dichotomy (default 30) */
   int max_iter;     /* cap on Lloyd assignment passes (default 100) */
-  int col_tile;     /* column-tile width of the recursion: 0 = automatic, else one of
-                       8, 16, 32, 64, 128 */
+  int col_tile;     /* column-tile width of the recursion: 0 = automatic (tiles of 8, 16, 32
+                       and 64 columns minimising sum (8 + w) over the tiles that cover the
+                       columns), else one of 8, 16, 32, 64, 128 for every tile */
   int checked;      /* nonzero: validate the CSR on csc_set_graph (device input too) */
   int timing;       /* nonzero: time the Chebyshev step launches with CUDA events on the
                        context stream (read with csc_get_stats) */
@@ -88,7 +89,8 @@ typedef struct csc_stats {
   int64_t step_launches;  /* general Chebyshev step launches bracketed by timing events */
   double step_ms;         /* device time of those launches (ms), CUDA events on the context stream */
   int64_t filter_passes;  /* recursion passes (one per column tile per filtering call) */
-  int64_t tile;           /* column-tile width of the last filtering pass */
+  int64_t tile;           /* widest column tile of the last filtering pass (a pass covers its
+                             columns with tiles of 8, 16, 32 or 64; see csc_opts.col_tile) */
   int64_t batched_launches; /* persistent batched kernel launches (direct or in a graph) */
   int64_t graph_replays;    /* batched launches replayed from a captured CUDA graph */
   int64_t autotune_trials;  /* candidate tile timings run by the batched-path autotuner */
@@ -96,6 +98,10 @@ typedef struct csc_stats {
   int64_t kmeans_passes;    /* k-means assignment passes */
   int64_t kmeans_near_ties; /* rows whose distance-pass margin was within its error bound and
                                were re-decided exactly (summed over passes) */
+  double step_bytes;        /* algorithmic bytes of the timed step launches: per launch over a
+                               tile of width w, 4 nnz (col_idx; 8 nnz when weighted) + 8 (n+1)
+                               (row_ptr) + 4 n (D^-1/2) + n w (s + 4 + 4 + 8) (V_{j-1} of s bytes
+                               per value, V_j, V_{j+1}, Psi read and write) */
 } csc_stats;
 
 /* ---------------------------------------------------------------- library */

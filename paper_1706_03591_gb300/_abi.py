@@ -42,6 +42,7 @@ class csc_stats(C.Structure):
         ("batched_waves", C.c_int64),
         ("kmeans_passes", C.c_int64),
         ("kmeans_near_ties", C.c_int64),
+        ("step_bytes", C.c_double),
     ]
 
 

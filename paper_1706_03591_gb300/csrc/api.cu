@@ -188,15 +188,41 @@ csc_status fail(csc_ctx* ctx, csc_status s, const std::string& msg) {
     if (!(expr)) return fail(ctx, CSC_ENOMEM, "device allocation failed: " #expr); \
   } while (0)
 
-int tile_width(const csc_ctx* ctx, int64_t n, int c) {
-  if (ctx->opts.col_tile > 0) return ctx->opts.col_tile;
-  // Narrowest tile that covers c, capped at 64 (fewer launches), then halved while the gathered
-  // block n x w floats exceeds 128 MB: at n = 1e6 a 32-column tile measured fastest per column,
-  // ahead of 64 (L2 misses) and 16 (L2-bound gathers); small graphs keep wide tiles.
-  int w = 8;
-  while (w < 64 && w < c) w *= 2;
-  while (w > 8 && (double)n * w * 4.0 > 128.0 * (1 << 20)) w /= 2;
-  return w;
+// Column tiles of a filtering pass over c columns: widths in {8, 16, 32, 64} covering c, chosen to
+// minimise sum_i (kTileFixed + w_i).  A step launch costs a part that does not depend on its width
+// (the per-row staging, own-row loads and epilogue) plus a part proportional to it: on the
+// power-law graph at n = 8e6 a launch took 2.7, 3.6, 5.3 and 8.4 ms at w = 8, 16, 32 and 64, on
+// the SBM at n = 1e6 0.30, 0.53 and 0.96 ms at w = 16, 32 and 64, so wide tiles are cheaper per
+// column on both, and a small remainder takes its own narrow tile.  col_tile > 0 forces one width.
+constexpr int kTileFixed = 8;
+std::vector<int> tile_plan(const csc_ctx* ctx, int c) {
+  if (ctx->opts.col_tile > 0) return std::vector<int>((c + ctx->opts.col_tile - 1) / ctx->opts.col_tile, ctx->opts.col_tile);
+  static const int widths[4] = {64, 32, 16, 8};
+  std::vector<int> cost(c + 1, 0), pick(c + 1, 8);
+  for (int r = 1; r <= c; ++r) {
+    cost[r] = INT32_MAX;
+    for (int w : widths) {  // widest first: ties keep the fewer, wider tiles
+      const int v = kTileFixed + w + cost[std::max(0, r - w)];
+      if (v < cost[r]) { cost[r] = v; pick[r] = w; }
+    }
+  }
+  std::vector<int> plan;
+  for (int r = c; r > 0; r -= pick[r]) plan.push_back(pick[r]);
+  std::sort(plan.begin(), plan.end(), [](int x, int y) { return x > y; });
+  return plan;
+}
+
+int plan_columns(const std::vector<int>& plan) {
+  int t = 0;
+  for (int w : plan) t += w;
+  return t;
+}
+
+// Algorithmic bytes of one general step launch over a tile of width w (SURVEY-style forward form):
+// col_idx (+ weights), row_ptr, D^-1/2, V_{j-1} (s_prev bytes per value), V_j once, V_{j+1}, and Psi
+// read and write.
+double step_launch_bytes(int64_t n, int64_t nnz, bool weighted, int w, int s_prev) {
+  return 4.0 * nnz * (weighted ? 2 : 1) + 8.0 * (n + 1) + 4.0 * n + (double)n * w * (s_prev + 4 + 4 + 8);
 }
 
 bool valid_tile(int w) { return w == 8 || w == 16 || w == 32 || w == 64 || w == 128; }
@@ -219,13 +245,14 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
                       int64_t ldp) {
   const int64_t n = ctx->g.n;
   cudaStream_t s = ctx->stream;
-  const int w = tile_width(ctx, n, c);
-  if (!valid_tile(w)) return fail(ctx, CSC_EINVAL, "col_tile must be 8, 16, 32, 64 or 128");
-  const int ntiles = (c + w - 1) / w;
-  const int grid = csc::cheb_grid(w);
-  ctx->last_tile = w;
+  const std::vector<int> plan = tile_plan(ctx, c);
+  const int wmax = plan.empty() ? 8 : plan.front();
+  if (!valid_tile(wmax)) return fail(ctx, CSC_EINVAL, "col_tile must be 8, 16, 32, 64 or 128");
+  const int ntiles = (int)plan.size();
+  const int grid = csc::cheb_grid(wmax);
+  ctx->last_tile = wmax;
   const int rows = 2 * m + 1;
-  for (auto& b : ctx->tbuf) ALLOC_OK(csc::ensure(b, (size_t)std::max<int64_t>(n, 1) * w * 4));
+  for (auto& b : ctx->tbuf) ALLOC_OK(csc::ensure(b, (size_t)std::max<int64_t>(n, 1) * wmax * 4));
   ALLOC_OK(csc::ensure(ctx->part, (size_t)ntiles * rows * grid * 8));
   ALLOC_OK(csc::ensure(ctx->ef, (size_t)rows * 8));
   ALLOC_OK(csc::ensure(ctx->coef, (size_t)(m + 1) * 4));
@@ -244,8 +271,9 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
   }
   const float inv_sqrt_d = (float)(1.0 / std::sqrt((double)src.d));
   double* part = csc::as<double>(ctx->part);
-  for (int tile = 0; tile < ntiles; ++tile) {
-    const int c0 = tile * w;
+  int c0 = 0;
+  for (int tile = 0; tile < ntiles; c0 += plan[tile], ++tile) {
+    const int w = plan[tile];
     const int valid = std::min(w, c - c0);
     // signals and caller blocks are in the caller's node order; the tile in the internal order
     const int32_t* to_caller = ctx->g.permuted ? csc::as<int32_t>(ctx->g.perm) : nullptr;
@@ -287,7 +315,12 @@ csc_status run_filter(csc_ctx* ctx, int m, double lambda_c, int c, const Source&
       sa.tp_unscaled = j == 1;
       CUDA_OK(csc::launch_cheb_step(sa, j == 1 ? t0_dtype : CSC_F32, grid, s));
     }
-    if (timed) CUDA_OK(cudaEventRecord(ctx->events[2 * tile + 1], s));
+    if (timed) {
+      CUDA_OK(cudaEventRecord(ctx->events[2 * tile + 1], s));
+      for (int j = 1; j < m; ++j)
+        ctx->step_bytes += step_launch_bytes(n, ctx->g.nnz, ctx->g.weighted, w,
+                                             j == 1 && t0_dtype == CSC_BF16 ? 2 : 4);
+    }
     ctx->launches += m + 1;
     ctx->filter_passes += 1;
   }
@@ -502,11 +535,13 @@ csc_status csc_get_stats(csc_ctx* ctx, csc_stats* out, int reset) {
   out->batched_waves = ctx->batched_waves;
   out->kmeans_passes = ctx->kmeans_passes;
   out->kmeans_near_ties = ctx->kmeans_near_ties;
+  out->step_bytes = ctx->step_bytes;
   if (reset) {
     ctx->launches = ctx->step_launches = ctx->filter_passes = 0;
     ctx->batched_launches = ctx->graph_replays = ctx->autotune_trials = 0;
     ctx->kmeans_passes = ctx->kmeans_near_ties = 0;
     ctx->step_ms = 0.0;
+    ctx->step_bytes = 0.0;
   }
   return CSC_OK;
 }
@@ -700,8 +735,7 @@ csc_status csc_cheb_filter(csc_ctx* ctx, int m, double lambda_c, const void* R, 
     src.R = R;
     src.ldr = ldr;
   }
-  const int w = tile_width(ctx, n, c);
-  const int cpad = ((c + w - 1) / w) * w;
+  const int cpad = plan_columns(tile_plan(ctx, c));
   float* psi = nullptr;
   if (psi_out) {
     ALLOC_OK(csc::ensure(ctx->psi, (size_t)n * cpad * 4));
@@ -828,8 +862,7 @@ csc_status filter_snapshot(csc_ctx* ctx, int m, int d, int dp, uint64_t seed, in
   } else if (lam < 0) {
     lam = ctx->lambda;
   }
-  const int w = tile_width(ctx, n, c);
-  const int cpad = ((c + w - 1) / w) * w;
+  const int cpad = plan_columns(tile_plan(ctx, c));
   ALLOC_OK(csc::ensure(ctx->psi, (size_t)n * cpad * 4));
   csc_status st = run_filter(ctx, m, lam, c, src, csc::as<float>(ctx->psi), cpad);
   if (st != CSC_OK) return st;
@@ -1179,8 +1212,7 @@ csc_status csc_compressive_cluster(csc_ctx* ctx, const float* theta, const void*
   const int32_t* labels = csc::as<int32_t>(cs.labels) + (size_t)pick * n_omega;
 
   // 3. interpolation: X = h(L) Z, one filtering of each cluster's weighted indicator
-  const int w = tile_width(ctx, n, k);
-  const int cpad = ((k + w - 1) / w) * w;
+  const int cpad = plan_columns(tile_plan(ctx, k));
   ALLOC_OK(csc::ensure(cs.z, (size_t)n * k * 4));
   ALLOC_OK(csc::ensure(cs.x, (size_t)n * cpad * 4));
   ALLOC_OK(csc::ensure(cs.assign, (size_t)n * 4));

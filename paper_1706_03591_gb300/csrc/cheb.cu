@@ -397,8 +397,8 @@ __device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, dou
 // A CTA walks its blocks in chunks: one coalesced load of the row offsets (one per thread) finds
 // the longest run of rows whose edges fit the shared-memory buffer, and their column indices
 // and edge weights are staged there.  Each row of a chunk is reduced by spr slots of LPR lanes
-// (spr a power of two chosen from the chunk's largest degree, so that a long row spreads over
-// up to a whole warp while short rows keep one slot each); the slots stride over the row's
+// (spr the smallest power of two with 64 spr >= the chunk's largest degree, so that a long row
+// spreads over up to a whole warp while short rows keep one slot each); the slots stride over the row's
 // edges with kRowUnroll 16-byte loads in flight per lane and are folded with xor shuffles in a
 // fixed order.  A row too long for the buffer on its own (a hub) is reduced by the whole CTA
 // straight from global memory: every slot of every warp strides over its edges, the warps
@@ -408,7 +408,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, dou
 
 constexpr int kChunkRows = kBlock - 1;  // at most one row offset per thread
 constexpr int kChunkEdges = 5632;       // staged columns and weights: 45 KB
-constexpr int kEdgesPerSlot = 32;       // spr: smallest power of two with spr * 32 >= max degree
+constexpr int kEdgesPerSlot = 64;       // spr: smallest power of two with spr * 64 >= max degree
 
 struct StageChunk {
   union {
@@ -689,10 +689,11 @@ __device__ __forceinline__ void coop_row(const StepArgs& a, StageChunk& st, int6
 
 // FIRST: T_1 = L~ T_0 (stored as V_1 = vs T_1), Psi = a_0 T_0 + a_1 T_1, partials <T0,T0>,
 // <T1,T1>, <T1,T0> (TG: storage type of T_0).  Else one general step (TP: storage type of
-// T_{j-1}), partials <T_{j+1},T_{j+1}>, <T_{j+1},T_j>.  Four CTAs per SM (at most 64 registers
-// per thread) keep more gathers in flight.
+// T_{j-1}), partials <T_{j+1},T_{j+1}>, <T_{j+1},T_j>.  Three CTAs per SM (at most 85 registers
+// per thread): at four (64 registers) the gather batch and the own-row operands spilled, and
+// the spill traffic cost more than the extra warps gained.
 template <int LPR, bool FIRST, typename TG, typename TP>
-__global__ void __launch_bounds__(kBlock, 4) cheb_rows_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) cheb_rows_kernel(StepArgs a) {
   constexpr int NQ = FIRST ? 3 : 2;
   __shared__ StageChunk st;
   double acc[NQ];
@@ -936,10 +937,10 @@ cudaError_t launch_cheb_first(const StepArgs& a, int t0_dtype, int grid, cudaStr
 
 cudaError_t launch_cheb_step(const StepArgs& a, int tp_dtype, int grid, cudaStream_t s) {
   const int lpr = a.w / 4;
-  const void* fn = tp_dtype == CSC_BF16 ? rows_kernel_for<false, float, __nv_bfloat16>(lpr)
-                                        : rows_kernel_for<false, float, float>(lpr);
   StepArgs b = a;
   b.l2pf = (double)a.n * a.w * 4.0 > 64.0 * (1 << 20);
+  const void* fn = tp_dtype == CSC_BF16 ? rows_kernel_for<false, float, __nv_bfloat16>(lpr)
+                                        : rows_kernel_for<false, float, float>(lpr);
   return launch_any(fn, b, grid, s);
 }
 

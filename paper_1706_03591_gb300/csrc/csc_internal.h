@@ -353,6 +353,7 @@ struct csc_ctx {
   // counters (csc_get_stats)
   int64_t launches = 0, step_launches = 0, filter_passes = 0;
   double step_ms = 0.0;
+  double step_bytes = 0.0;  // algorithmic bytes of the timed step launches
   int last_tile = 0;
   std::vector<cudaEvent_t> events;  // timing event pairs, one per column tile
   // batched filtering (batched.cu)

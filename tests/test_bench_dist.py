@@ -55,4 +55,3 @@ def test_single_rank_defaults(monkeypatch):
     assert bench.dist_env() == (0, 1, 0)
     d = bench.Dist(1)
     assert d.reduce(3.5, "max") == 3.5
-    assert bench.step_bytes(10, 20, 8) == 4 * 20 + 8 * 11 + 4 * 10 + 5 * 4 * 10 * 8

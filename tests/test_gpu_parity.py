@@ -504,3 +504,24 @@ def test_algorithm1_similarity_policy_parity(gpu_lib):
             prev = cur
     # the sequence exercised a reduced reuse, full reuse and both check outcomes
     assert len(cols_seen) >= 3 and checks_seen == {True, False}
+
+
+@pytest.mark.parametrize("c,tiles", [(39, [32, 8]), (64, [64]), (13, [16]), (192, [64, 64, 64])])
+def test_tile_plan_and_step_byte_accounting(gpu_lib, cfg1_graph, c, tiles):
+    """The automatic plan covers c columns with tiles of 8..64 minimising sum (8 + w), and the
+    library's step_bytes count every timed step launch at its own width."""
+    g = cfg1_graph
+    m = 6
+    r = W.gaussian_block(g.n, c, 64, seed=c)
+    lt = lp.shifted_laplacian(g.n, g.row_ptr, g.col_idx)
+    with gpu_lib.Context({"timing": 1}) as ctx:
+        upload_graph(ctx, g)
+        psi = torch.zeros((g.n, c), device="cuda")
+        ctx.stats(reset=True)
+        ctx.cheb_filter(m, 0.5, dev(r), psi)
+        st = ctx.stats()
+    assert rel(psi.cpu().numpy(), cb.cheb_filter(lt, r.astype(np.float64), m, 0.5)) < FP32_TOL
+    assert st["tile"] == max(tiles) and st["filter_passes"] == len(tiles)
+    assert st["step_launches"] == len(tiles) * (m - 1)
+    per = lambda w: 4.0 * g.nnz + 8.0 * (g.n + 1) + 4.0 * g.n + g.n * w * (4 + 4 + 4 + 8)
+    assert st["step_bytes"] == pytest.approx((m - 1) * sum(per(w) for w in tiles), rel=1e-12)
