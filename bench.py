@@ -50,6 +50,8 @@ CL = dict(name="chung_lu_8e6", n=8_000_000, exponent=2.5, deg=25.0, k=64, mixing
 SBM = dict(name="sbm_1e6", n=1_000_000, k=100, deg=30.0, ratio=10.0, zipf=0.8, d=256, m=100, p=0.75,
            churn=0.005, precision=0)
 CPU_ORDER = 16   # Chebyshev steps per column in the bounded CPU samples
+ORDERS = {0: "caller order", 1: "library order: degrees descending",
+          2: "library order: degrees descending, regrouped by the first clustering"}
 
 
 def args_parse():
@@ -63,6 +65,9 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="column-tile width (0 = library default)")
+    ap.add_argument("--reorder", type=int, default=2,
+                    help="node order of the library for the power-law workload (0 caller, 1 degrees, "
+                         "2 degrees then grouped by the first clustering)")
     ap.add_argument("--no-sbm", action="store_true", help="skip the n = 1e6 SBM sequence")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-grad", action="store_true", help="skip the differentiation timing")
@@ -561,7 +566,7 @@ def run_ours(a, rank, world, local):
     graphs, nnz, labels = cl_sequence(count, seed, n, "cuda")
     inits = [W.forgy_indices(n, CL["k"], seed=seed + t) for t in range(count)]
     clocks = Clocks(local)
-    opts = {"timing": 1, "col_tile": a.tile, "precision": CL["precision"]}
+    opts = {"timing": 1, "col_tile": a.tile, "precision": CL["precision"], "reorder": a.reorder}
     ctx = csc.Context(opts)
     assign = torch.zeros(n, dtype=torch.int32, device="cuda")
     ms, units, info, clk, phases = run_sequence(ctx, CL, n, graphs, nnz, seed, inits, assign, a.warmup,
@@ -614,7 +619,7 @@ def run_ours(a, rank, world, local):
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 signals, f32 recursion, f64 sums",
         "data": "synthetic",
-        "config": workload_config(CL, n, tile),
+        "config": {**workload_config(CL, n, tile), "node_order": ORDERS[a.reorder]},
         "roofline": roofline(stats, n, nnz_timed, tile, CL["name"] if n == CL["n"] else f"chung_lu_{n}"),
         "cpu_baseline": base,
         "e2e": e2e,

@@ -79,8 +79,11 @@ typedef struct csc_opts {
                        degrees descending (ties by node id), so that the rows a block of the
                        recursion handles have similar degrees and the most gathered rows are
                        contiguous; the order is fixed at the first csc_set_graph of a feature
-                       ring and every row-indexed input and output of the ABI stays in the
-                       caller's node order.  0: the caller's order. */
+                       ring.  2: the same, and at the first csc_set_graph after a csc_cluster
+                       the rows are regrouped once by that assignment (degrees descending within
+                       a cluster; the ring moves with them), so that most gathers of a block stay
+                       inside one cluster's rows.  0: the caller's order.  Every row-indexed input
+                       and output of the ABI stays in the caller's node order. */
 } csc_opts;
 
 /* Counters of a context (csc_get_stats). */

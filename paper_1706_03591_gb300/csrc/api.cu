@@ -364,19 +364,31 @@ bool valid_where(int where) { return where == CSC_HOST || where == CSC_DEVICE; }
 
 // Node order of the internal graph: degrees descending, ties by caller id (a stable counting
 // sort, O(n + max degree)).  perm[i] = caller row of internal row i, iperm its inverse.
-void degree_order(int64_t n, const int64_t* rp, std::vector<int32_t>& perm, std::vector<int32_t>& iperm) {
+// With labels (label[u] in [0, k) for caller row u): grouped by label first, degrees descending
+// within a label (a stable counting sort by degree, then a stable one by label).
+void degree_order(int64_t n, const int64_t* rp, const int32_t* label, int k, std::vector<int32_t>& perm,
+                  std::vector<int32_t>& iperm) {
   int64_t maxdeg = 0;
   for (int64_t u = 0; u < n; ++u) maxdeg = std::max(maxdeg, rp[u + 1] - rp[u]);
   std::vector<int64_t> start(maxdeg + 2, 0);
   for (int64_t u = 0; u < n; ++u) start[maxdeg - (rp[u + 1] - rp[u]) + 1] += 1;
   for (int64_t b = 1; b <= maxdeg + 1; ++b) start[b] += start[b - 1];
+  std::vector<int32_t> by_degree(n);
+  for (int64_t u = 0; u < n; ++u) by_degree[start[maxdeg - (rp[u + 1] - rp[u])]++] = (int32_t)u;
   perm.assign(n, 0);
   iperm.assign(n, 0);
-  for (int64_t u = 0; u < n; ++u) {
-    const int64_t i = start[maxdeg - (rp[u + 1] - rp[u])]++;
-    perm[i] = (int32_t)u;
-    iperm[u] = (int32_t)i;
+  if (label == nullptr) {
+    perm = by_degree;
+  } else {
+    std::vector<int64_t> lstart(k + 1, 0);
+    for (int64_t u = 0; u < n; ++u) lstart[label[u] + 1] += 1;
+    for (int b = 1; b <= k; ++b) lstart[b] += lstart[b - 1];
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t u = by_degree[i];
+      perm[lstart[label[u]]++] = u;
+    }
   }
+  for (int64_t i = 0; i < n; ++i) iperm[perm[i]] = (int32_t)i;
 }
 
 csc_status validate_host_csr(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rp,
@@ -417,6 +429,54 @@ csc_status copy_out(csc_ctx* ctx, const void* src, int src_dtype, int64_t ld_src
     CUDA_OK(cudaMemcpy2DAsync(dst, ld_dst * esz, ctx->out_stage.ptr, d * esz, d * esz, n,
                               cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));
+  return CSC_OK;
+}
+
+// New internal order grouped by the previous assignment (reorder = 2); permutes the feature ring,
+// its row-normalised copy and the previous assignment into it.  The caller's CSR of the snapshot
+// being loaded (host or device row_ptr) gives the degrees.
+csc_status regroup_by_clusters(csc_ctx* ctx, int64_t n, const int64_t* row_ptr, int where) {
+  csc::Graph& g = ctx->g;
+  cudaStream_t s = ctx->stream;
+  std::vector<int64_t> rp_host;
+  const int64_t* rp = row_ptr;
+  if (where == CSC_DEVICE) {
+    rp_host.resize(n + 1);
+    CUDA_OK(cudaMemcpyAsync(rp_host.data(), row_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost, s));
+  }
+  std::vector<int32_t> lab_int(n), lab(n);
+  CUDA_OK(cudaMemcpyAsync(lab_int.data(), ctx->prev_assign.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (where == CSC_DEVICE) rp = rp_host.data();
+  for (int64_t u = 0; u < n; ++u) lab[u] = lab_int[g.h_iperm[u]];
+  std::vector<int32_t> perm, iperm;
+  degree_order(n, rp, lab.data(), ctx->prev_k, perm, iperm);
+  // old internal row of each new internal row
+  std::vector<int32_t> from(n);
+  for (int64_t i = 0; i < n; ++i) from[i] = g.h_iperm[perm[i]];
+  const int d = ctx->ring_d;
+  const size_t ysz = dtype_size(ctx->opts.precision);
+  ALLOC_OK(csc::ensure(ctx->out_stage, (size_t)n * d * 4));
+  ALLOC_OK(csc::ensure(ctx->astage, (size_t)n * 4));
+  ALLOC_OK(csc::ensure(g.perm, (size_t)n * 4));
+  ALLOC_OK(csc::ensure(g.iperm, (size_t)n * 4));
+  CUDA_OK(cudaMemcpyAsync(g.iperm.ptr, from.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));  // map (scratch)
+  const int32_t* map = csc::as<int32_t>(g.iperm);
+  // the ring, its normalised copy and the previous assignment move with the rows
+  CUDA_OK(csc::launch_convert(ctx->theta.ptr, CSC_F32, d, ctx->out_stage.ptr, CSC_F32, d, n, d, s, map));
+  CUDA_OK(cudaMemcpyAsync(ctx->theta.ptr, ctx->out_stage.ptr, (size_t)n * d * 4, cudaMemcpyDeviceToDevice, s));
+  CUDA_OK(csc::launch_convert(ctx->y.ptr, ctx->opts.precision, d, ctx->out_stage.ptr, ctx->opts.precision, d, n, d,
+                              s, map));
+  CUDA_OK(cudaMemcpyAsync(ctx->y.ptr, ctx->out_stage.ptr, (size_t)n * d * ysz, cudaMemcpyDeviceToDevice, s));
+  CUDA_OK(csc::launch_gather_i32(csc::as<int32_t>(ctx->astage), csc::as<int32_t>(ctx->prev_assign), map, n, s));
+  CUDA_OK(cudaMemcpyAsync(ctx->prev_assign.ptr, ctx->astage.ptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  CUDA_OK(cudaMemcpyAsync(g.perm.ptr, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemcpyAsync(g.iperm.ptr, iperm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  g.h_perm = std::move(perm);
+  g.h_iperm = std::move(iperm);
+  ctx->launches += 3;
+  ctx->grouped = true;
   return CSC_OK;
 }
 
@@ -479,7 +539,7 @@ csc_status csc_create(csc_ctx** out, const csc_opts* opts, void* cuda_stream) {
   if (opts) o = *opts;
   if (!valid_dtype(o.precision) || o.max_bisect < 1 || o.max_iter < 1 ||
       (o.col_tile != 0 && !valid_tile(o.col_tile)) || (o.estimator != 0 && o.estimator != 1) ||
-      (o.reorder != 0 && o.reorder != 1))
+      (o.reorder < 0 || o.reorder > 2))
     return CSC_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -623,12 +683,19 @@ csc_status csc_set_graph(csc_ctx* ctx, int64_t n, int64_t nnz, const int64_t* ro
         CUDA_OK(cudaStreamSynchronize(s));
         rp = rp_host.data();
       }
-      degree_order(n, rp, g.h_perm, g.h_iperm);
+      degree_order(n, rp, nullptr, 0, g.h_perm, g.h_iperm);
       ALLOC_OK(csc::ensure(g.perm, (size_t)n * 4));
       ALLOC_OK(csc::ensure(g.iperm, (size_t)n * 4));
       CUDA_OK(cudaMemcpyAsync(g.perm.ptr, g.h_perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
       CUDA_OK(cudaMemcpyAsync(g.iperm.ptr, g.h_iperm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
       CUDA_OK(cudaStreamSynchronize(s));  // the host vectors may be reallocated later
+      ctx->grouped = false;
+    } else if (ctx->opts.reorder == 2 && !ctx->grouped && ctx->has_prev && ctx->prev_k > 0) {
+      // once, after the first clustering: rows grouped by the previous assignment (degrees
+      // descending within a cluster), so that a block's gathers mostly stay inside one cluster's
+      // rows; the ring and the previous assignment move with the rows
+      csc_status st = regroup_by_clusters(ctx, n, row_ptr, where);
+      if (st != CSC_OK) return st;
     }
     ALLOC_OK(csc::ensure(ctx->gtmp, ((size_t)n + (size_t)csc::scan_sums_len(n)) * 8));
     long long* tmp = csc::as<long long>(ctx->gtmp);
@@ -1282,6 +1349,7 @@ csc_status csc_save_state(csc_ctx* ctx, const char* path) {
   const int64_t t = ctx->t, next_id = ctx->next_id;
   // the ring's rows are stored in the context's node order, which is saved with them
   const int32_t permuted = ctx->g.permuted && (int64_t)ctx->g.h_perm.size() == n ? 1 : 0;
+  const int32_t grouped = ctx->grouped ? 1 : 0;
   const bool ok = put(sf.f, kStateMagic, 8) && put(sf.f, &kStateVersion, 4) && put(sf.f, &precision, 4) &&
                   put(sf.f, &n, 8) && put(sf.f, &ring_d, 4) && put(sf.f, &t, 8) && put(sf.f, &next_id, 8) &&
                   put(sf.f, &has_lambda, 4) && put(sf.f, &ctx->lambda, 8) && put(sf.f, &last_m, 4) &&
@@ -1289,7 +1357,8 @@ csc_status csc_save_state(csc_ctx* ctx, const char* path) {
                   put(sf.f, ctx->stamp.data(), ctx->stamp.size() * 8) && put(sf.f, &has_prev, 4) &&
                   put(sf.f, &prev_k, 4) && put(sf.f, theta.data(), cells * 4) && put(sf.f, y.data(), y.size()) &&
                   put(sf.f, prev.data(), prev.size() * 4) && put(sf.f, &ctx->rho_since, 8) &&
-                  put(sf.f, &permuted, 4) && put(sf.f, ctx->g.h_perm.data(), permuted ? (size_t)n * 4 : 0);
+                  put(sf.f, &permuted, 4) && put(sf.f, &grouped, 4) &&
+                  put(sf.f, ctx->g.h_perm.data(), permuted ? (size_t)n * 4 : 0);
   const bool closed = fclose(sf.f) == 0;
   sf.f = nullptr;
   if (!ok || !closed) return fail(ctx, CSC_EINVAL, std::string("csc_save_state: write failed for ") + path);
@@ -1330,10 +1399,10 @@ csc_status csc_load_state(csc_ctx* ctx, const char* path) {
   std::vector<unsigned char> y(cells * ysz);
   std::vector<int32_t> prev(has_prev ? (size_t)n : 0);
   double rho_since = 0.0;
-  int32_t permuted = 0;
+  int32_t permuted = 0, grouped = 0;
   ok = get(sf.f, theta.data(), cells * 4) && get(sf.f, y.data(), y.size()) && get(sf.f, prev.data(), prev.size() * 4) &&
-       get(sf.f, &rho_since, 8) && get(sf.f, &permuted, 4);
-  if (!ok || (permuted != 0 && permuted != 1) || !(rho_since >= 0.0))
+       get(sf.f, &rho_since, 8) && get(sf.f, &permuted, 4) && get(sf.f, &grouped, 4);
+  if (!ok || (permuted != 0 && permuted != 1) || (grouped != 0 && grouped != 1) || !(rho_since >= 0.0))
     return fail(ctx, CSC_EINVAL, "csc_load_state: truncated file");
   if ((permuted != 0) != (ctx->opts.reorder != 0))
     return fail(ctx, CSC_EINVAL, "csc_load_state: the state was saved with another reorder setting");
@@ -1367,6 +1436,7 @@ csc_status csc_load_state(csc_ctx* ctx, const char* path) {
   ctx->g.h_perm = std::move(perm);
   ctx->g.h_iperm = std::move(iperm);
   ctx->rho_since = rho_since;
+  ctx->grouped = grouped != 0;
   ctx->ring_n = n;
   ctx->ring_d = ring_d;
   ctx->t = t;

@@ -345,6 +345,7 @@ struct csc_ctx {
   csc::DevBuf prev_assign;
   int prev_k = 0;
   bool has_prev = false;
+  bool grouped = false;    // reorder = 2: rows grouped by an assignment
   csc::DevBuf ystage;      // caller features staged on the device
   csc::DevBuf astage;      // caller assignment staged on the device
   csc::DevBuf out_stage;   // conversions before a host copy

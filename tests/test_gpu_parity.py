@@ -345,7 +345,7 @@ def test_kmeans_exact_ties_lowest_index(gpu_lib):
     np.testing.assert_array_equal(out["assign"], lab_ref)
 
 
-@pytest.mark.parametrize("reorder", [1, 0])
+@pytest.mark.parametrize("reorder", [1, 0, 2])
 def test_algorithm1_dynamic_parity_cfg1(gpu_lib, cfg1_graph, reorder):
     """SBM n=2000, k=10, degree 20, d=64, m=50, 1% rewiring per step, p=0.5: 1 + 5 snapshots."""
     n, k, d, m, p, seed = 2000, 10, 64, 50, 0.5, 2024

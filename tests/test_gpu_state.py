@@ -27,7 +27,7 @@ def _snapshot(ctx, g, t, n, k, d, m, p, seed):
     return lam, cnt, assign, theta
 
 
-@pytest.mark.parametrize("precision,reorder", [(0, 1), (1, 1), (0, 0)])
+@pytest.mark.parametrize("precision,reorder", [(0, 1), (1, 1), (0, 0), (0, 2)])
 def test_resume_continues_the_sequence_exactly(gpu_lib, tmp_path, precision, reorder):
     n, k, d, m, p, seed = 2000, 10, 64, 50, 0.5, 11
     g0 = W.sbm_graph(n, k, 20, 10, seed=1)
