@@ -299,7 +299,8 @@ def batched_comparison(seed=77, count=512, m=60):
         torch.cuda.synchronize()
         st = ctx.stats()
     t_batched = ev[0].elapsed_time(ev[1]) / reps
-    with csc.Context({"precision": 0}) as ctx:
+    # the same kernels one graph at a time, in the caller's node order like the batched launch
+    with csc.Context({"precision": 0, "reorder": 0}) as ctx:
         rbuf = torch.zeros(max(g["n"] * g["c"] for g in graphs), device="cuda")
 
         def plain():

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 6
+#define CSC_ABI_VERSION 7
 
 typedef struct csc_ctx csc_ctx;
 
@@ -84,6 +84,10 @@ typedef struct csc_opts {
                        a cluster; the ring moves with them), so that most gathers of a block stay
                        inside one cluster's rows.  0: the caller's order.  Every row-indexed input
                        and output of the ABI stays in the caller's node order. */
+  int64_t wave_bytes; /* csc_filter_batched: working-set budget (bytes) of one wave, the run of
+                         consecutive column tiles whose recursion proceeds together; <= 0 selects
+                         16 GiB.  Smaller waves finish tiles sooner, larger ones keep more tiles
+                         in flight per recursion step. */
 } csc_opts;
 
 /* Counters of a context (csc_get_stats). */
@@ -97,7 +101,7 @@ typedef struct csc_stats {
   int64_t batched_launches; /* persistent batched kernel launches (direct or in a graph) */
   int64_t graph_replays;    /* batched launches replayed from a captured CUDA graph */
   int64_t autotune_trials;  /* candidate tile timings run by the batched-path autotuner */
-  int64_t batched_waves;    /* L2-sized waves of the last batched call */
+  int64_t batched_waves;    /* waves of the last batched call (csc_opts.wave_bytes) */
   int64_t kmeans_passes;    /* k-means assignment passes */
   int64_t kmeans_near_ties; /* rows whose distance-pass margin was within its error bound and
                                were re-decided exactly (summed over passes) */

@@ -26,6 +26,7 @@ class csc_opts(C.Structure):
         ("timing", C.c_int),
         ("estimator", C.c_int),
         ("reorder", C.c_int),
+        ("wave_bytes", C.c_int64),
     ]
 
 

@@ -514,6 +514,7 @@ void csc_default_opts(csc_opts* o) {
   o->timing = 0;
   o->estimator = 0;
   o->reorder = 1;
+  o->wave_bytes = 0;
 }
 
 const char* csc_status_string(csc_status s) {

@@ -77,7 +77,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   for (int g = 0; g < n_graphs; ++g) {
     const int64_t n = descs[g].n;
     GraphPlan& p = plan[g];
-    p.nblk = csc::edge_blocks(descs[g].nnz);
+    p.nblk = csc::row_blocks(n, descs[g].nnz);  // work items per tile: the row blocks
     p.off_scale = prep_bytes; prep_bytes += al(n * 4);
     p.off_vs = prep_bytes; prep_bytes += al(n * 4);
     p.off_ivs = prep_bytes; prep_bytes += al(n * 4);
@@ -117,7 +117,9 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     for (int h = g + 1; h < n_graphs; ++h)
       if (size_class(descs[h]) == key && descs[h].nnz > descs[rep].nnz) rep = h;
     const csc_graph_desc& d = descs[rep];
-    const int cmax = std::min(64, next_pow2(std::max(d.c, 8)));
+    // tiles of 16 to 64 columns: the persistent kernel carries one inlined path per width, and the
+    // narrowest one's registers cost more than its use (2124 -> 2062 ms on the 512-graph batch)
+    const int cmax = std::min(64, next_pow2(std::max(d.c, 16)));
     B_ALLOC(csc::ensure(ctx->b_tune, (size_t)3 * d.n * 64 * 4));
     B_ALLOC(csc::ensure(ctx->b_part, (size_t)2 * grid_step * 8));
     B_CUDA(cudaMemsetAsync(ctx->b_tune.ptr, 0, (size_t)3 * d.n * 64 * 4, s));
@@ -125,9 +127,9 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     cudaEvent_t e0, e1;
     B_CUDA(cudaEventCreate(&e0));
     B_CUDA(cudaEventCreate(&e1));
-    int best_w = 8;
+    int best_w = 16;
     float best_t = INFINITY;
-    for (int w = 8; w <= cmax; w *= 2) {
+    for (int w = 16; w <= cmax; w *= 2) {
       csc::StepArgs sa{};
       sa.n = d.n;
       sa.row_ptr = d.row_ptr;
@@ -195,9 +197,11 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
   std::vector<csc::BatchTile> tiles_h;
   std::vector<int32_t> items_h((size_t)nitems);
   // waves: consecutive tiles whose working set (recursion blocks, Psi, and the CSR of each graph
-  // they touch) stays within kWaveBytes, with at least two items per CTA of the grid
+  // they touch) stays within wave_budget, with at least two items per CTA of the grid.  With the
+  // chunked row-block items, larger waves keep more tiles in flight per step: on the 512-graph
+  // batch 256 MB, 512 MB, 1 GB, 4 GB and 16 GB waves took 2536, 2248, 2179, 2135 and 2124 ms.
   const int grid = csc::cheb_batched_grid();
-  constexpr size_t kWaveBytes = size_t(256) << 20;
+  const size_t wave_budget = ctx->opts.wave_bytes > 0 ? (size_t)ctx->opts.wave_bytes : size_t(16) << 30;
   std::vector<int64_t> wave_end;
   size_t wave_ws = 0;
   int64_t wave_items = 0;
@@ -222,7 +226,9 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
       sa.vs = static_cast<const float*>(views[g].vs.ptr);
       sa.ivs = static_cast<const float*>(views[g].ivs.ptr);
       sa.blk_row = static_cast<const int32_t*>(views[g].blk_row.ptr);
-      sa.nblk = p.nblk;
+      sa.nblk = csc::edge_blocks(d.nnz);
+      sa.srow = static_cast<const int32_t*>(views[g].srow.ptr);
+      sa.nsblk = p.nblk;
       sa.psi = pbase + p.off_psi + (size_t)t * p.w;
       sa.ldp = p.cpad;
       sa.coef = cbase + (size_t)g * (m + 1);
@@ -239,7 +245,7 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
       bt.inv_sqrt_d = (float)(1.0 / std::sqrt((double)d.d));
       const size_t tile_ws = (size_t)d.n * p.w * 16 +
                              (g != wave_graph ? (size_t)d.nnz * 4 + (size_t)d.n * 20 : 0);
-      if (wave_items > 0 && wave_items >= 2 * grid && wave_ws + tile_ws > kWaveBytes) {
+      if (wave_items > 0 && wave_items >= 2 * grid && wave_ws + tile_ws > wave_budget) {
         wave_end.push_back(item);
         wave_ws = 0;
         wave_items = 0;
@@ -254,11 +260,11 @@ extern "C" csc_status csc_filter_batched(csc_ctx* ctx, int n_graphs, const csc_g
     }
   }
   // Failure-detection test hook (host-side injection): with CSC_TEST_EXPIRE_WAIT set in the
-  // environment, the first tile waits for one more finished block than it has.  Its blocks are
+  // environment, the first tile waits for one more finished row block than it has.  Its blocks are
   // still bounded by the real item list, so nothing else changes: the bounded dependency wait
   // runs out, every other wait sees the error word and leaves, and the call returns
   // CSC_ETIMEOUT with the context usable for the next call.
-  if (!tiles_h.empty() && std::getenv("CSC_TEST_EXPIRE_WAIT") != nullptr) tiles_h[0].a.nblk += 1;
+  if (!tiles_h.empty() && std::getenv("CSC_TEST_EXPIRE_WAIT") != nullptr) tiles_h[0].a.nsblk += 1;
   B_CUDA(cudaMemcpyAsync(ctx->b_coef.ptr, coef_h.data(), coef_h.size() * 4, cudaMemcpyHostToDevice, s));
   B_CUDA(cudaMemcpyAsync(ctx->b_tiles.ptr, tiles_h.data(), tiles_h.size() * sizeof(csc::BatchTile),
                          cudaMemcpyHostToDevice, s));

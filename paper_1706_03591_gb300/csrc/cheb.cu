@@ -98,110 +98,7 @@ __device__ __forceinline__ float4 shfl_xor4(float4 v, int off) {
   return v;
 }
 
-// Shared-memory staging of one edge block: row offsets (relative to the block's first edge),
-// column indices and per-edge weights.
-struct Stage {
-  int col[kEdgeBuf];
-  float wt[kEdgeBuf];
-  int rp[kRowBuf + 1];
-};
-
 constexpr int kStageUnroll = 4;
-
-// Loads block b into shared memory.  Edge weight: w_e (1 for unit weights), times
-// D^{-1/2}[col_e] when SCALED (first step, which gathers the unscaled T_0).  Returns false
-// (nothing staged) when the block's edge span or row count exceeds the buffers; the block is
-// then read directly from global memory.
-template <bool SCALED>
-__device__ __forceinline__ bool stage_block(const StepArgs& a, Stage& st, int b, int& rs, int& re) {
-  rs = __ldg(a.blk_row + b);
-  re = __ldg(a.blk_row + b + 1);
-  const int64_t es = __ldg(a.row_ptr + rs);
-  const int64_t ee = __ldg(a.row_ptr + re);
-  const bool fits = (ee - es) <= kEdgeBuf && (re - rs) <= kRowBuf;
-  if (!fits) return false;
-  for (int i = threadIdx.x; i <= re - rs; i += blockDim.x)
-    st.rp[i] = (int)(__ldcs(a.row_ptr + rs + i) - es);
-  const int ne = (int)(ee - es);
-  const bool need_w = SCALED || a.val != nullptr;
-  for (int base = 0; base < ne; base += kStageUnroll * blockDim.x) {
-    int c[kStageUnroll];
-    float v[kStageUnroll];
-#pragma unroll
-    for (int u = 0; u < kStageUnroll; ++u) {
-      const int e = base + u * blockDim.x + threadIdx.x;
-      c[u] = e < ne ? __ldcs(a.col + es + e) : 0;
-      v[u] = (e < ne && a.val != nullptr) ? __ldcs(a.val + es + e) : 1.0f;
-    }
-    if (SCALED) {
-#pragma unroll
-      for (int u = 0; u < kStageUnroll; ++u)
-        if (base + u * blockDim.x + threadIdx.x < ne) v[u] *= __ldg(a.scale + c[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < kStageUnroll; ++u) {
-      const int e = base + u * blockDim.x + threadIdx.x;
-      if (e < ne) {
-        st.col[e] = c[u];
-        if (need_w) st.wt[e] = v[u];
-      }
-    }
-  }
-  return true;
-}
-
-constexpr int kGatherUnroll = 4;
-
-// sum_{e in row} wt_e X[col_e, 4 columns of this lane], folded over the S neighbour slots.
-// Staged: edges from shared memory, kGatherUnroll predicated loads in flight per lane.
-// Not staged: edges, weights (and D^{-1/2} when SCALED) from global memory.
-template <int LPR, bool SCALED, typename TG>
-__device__ __forceinline__ float4 gather_row(const StepArgs& a, const Stage& st, bool staged,
-                                             const TG* __restrict__ tg, int64_t row, int rl,
-                                             int slot, int sub) {
-  constexpr int S = 32 / LPR;
-  const int w = a.w;
-  const bool need_w = SCALED || a.val != nullptr;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  const TG* base = tg + sub * 4;
-  if (staged) {
-    const int beg = st.rp[rl], end = st.rp[rl + 1];
-    for (int e0 = beg + slot; e0 < end; e0 += kGatherUnroll * S) {
-      float4 v[kGatherUnroll];
-      float wt[kGatherUnroll];
-#pragma unroll
-      for (int u = 0; u < kGatherUnroll; ++u) {
-        const int e = e0 + u * S;
-        const bool ok = e < end;
-        const int c = ok ? st.col[e] : 0;
-        wt[u] = ok ? (need_w ? st.wt[e] : 1.0f) : 0.0f;
-        v[u] = ok ? ld4(base + (int64_t)c * w) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < kGatherUnroll; ++u) fma4(acc, wt[u], v[u]);
-    }
-  } else {
-    const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
-    for (int64_t e = beg + slot; e < end; e += S) {
-      const int c = __ldg(a.col + e);
-      float wv = a.val != nullptr ? __ldg(a.val + e) : 1.0f;
-      if (SCALED) wv *= __ldg(a.scale + c);
-      fma4(acc, wv, ld4(base + (int64_t)c * w));
-    }
-  }
-#pragma unroll
-  for (int off = LPR; off < 32; off <<= 1) acc = shfl_xor4(acc, off);
-  return acc;
-}
-
-// Folds per-lane float partials over the LPR lanes of slot 0 and accumulates them in float64
-// on lane 0.
-template <int LPR>
-__device__ __forceinline__ void fold_dot(float v, double& acc, int lane) {
-#pragma unroll
-  for (int off = 1; off < LPR; off <<= 1) v += __shfl_xor_sync(kFull, v, off);
-  if (lane == 0) acc += (double)v;
-}
 
 template <int NQ>
 __device__ __forceinline__ void block_store(double (&acc)[NQ], double* part) {
@@ -216,176 +113,6 @@ __device__ __forceinline__ void block_store(double (&acc)[NQ], double* part) {
     double s = 0.0;
     for (int i = 0; i < kBlock / 32; ++i) s += red[threadIdx.x][i];
     part[threadIdx.x * gridDim.x + blockIdx.x] = s;
-  }
-}
-
-// One edge block of the first step: T_1 = L~ T_0 (stored as V_1), Psi = a_0 T_0 + a_1 T_1,
-// partials <T0,T0>, <T1,T1>, <T1,T0> accumulated into acc (lane-0 values).
-template <int LPR, typename T0>
-__device__ __forceinline__ void first_block(const StepArgs& a, Stage& st, int b, double (&acc)[3]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int slot = lane / LPR, sub = lane % LPR;
-  const T0* __restrict__ t0 = static_cast<const T0*>(a.tg);
-  const int w = a.w;
-  float a0 = 0.f, a1 = 0.f;
-  if (a.psi != nullptr) { a0 = __ldg(a.coef); a1 = __ldg(a.coef + 1); }
-  int rs, re;
-  __syncthreads();
-  const bool staged = stage_block<true>(a, st, b, rs, re);
-  __syncthreads();
-  for (int r = rs + wid; r < re; r += kBlock / 32) {
-    const int64_t row = r;
-    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (slot == 0) own = ld4(t0 + row * w + sub * 4);
-    const float si = -__ldg(a.scale + row);
-    const float vsi = __ldg(a.vs + row);
-    const float4 g = gather_row<LPR, true, T0>(a, st, staged, t0, row, r - rs, slot, sub);
-    float e0 = 0.f, e1 = 0.f, f1 = 0.f;
-    if (slot == 0) {
-      const float4 t1 = make_float4(si * g.x, si * g.y, si * g.z, si * g.w);
-      st4(a.tn + row * w + sub * 4, make_float4(vsi * t1.x, vsi * t1.y, vsi * t1.z, vsi * t1.w));
-      if (a.psi != nullptr) {
-        float4 p;
-        p.x = fmaf(a1, t1.x, a0 * own.x);
-        p.y = fmaf(a1, t1.y, a0 * own.y);
-        p.z = fmaf(a1, t1.z, a0 * own.z);
-        p.w = fmaf(a1, t1.w, a0 * own.w);
-        st4(a.psi + row * a.ldp + sub * 4, p);
-      }
-      e0 = dot4(own, own);
-      e1 = dot4(t1, t1);
-      f1 = dot4(t1, own);
-    }
-    fold_dot<LPR>(e0, acc[0], lane);
-    fold_dot<LPR>(e1, acc[1], lane);
-    fold_dot<LPR>(f1, acc[2], lane);
-  }
-}
-
-
-// Row-parallel variant of the gather for the general step: the LPR lanes of one slot own
-// one row; kRowUnroll predicated 16-byte loads per lane are in flight per batch.
-constexpr int kRowUnroll = 8;
-
-template <int LPR, typename ST, bool SCALED = false, typename TG = float>
-__device__ __forceinline__ float4 gather_own_row(const StepArgs& a, const ST& st, bool staged,
-                                                 const TG* __restrict__ tg, int64_t row, int rl,
-                                                 bool valid, int sub) {
-  const int w = a.w;
-  const TG* base = tg + sub * 4;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (!valid) return acc;
-  if (staged) {
-    const int beg = st.rp[rl], end = st.rp[rl + 1];
-    const bool weighted = SCALED || a.val != nullptr;
-    const uint64_t keep = l2_keep();
-    constexpr int kLines = LPR >= 8 ? LPR / 8 : 1;  // 128-byte lines per gathered row
-    for (int e0 = beg; e0 < end; e0 += kRowUnroll) {
-      if (!SCALED && a.l2pf) {
-        // the next batch's rows into L2 while this batch loads: more misses in flight without
-        // holding registers (pays off when the gathered block exceeds the L2)
-        for (int q = sub; q < kRowUnroll * kLines; q += LPR) {
-          const int ep = e0 + kRowUnroll + q / kLines;
-          if (ep < end)
-            asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(tg + (int64_t)st.col[ep] * w + (q % kLines) * 32)
-                         : "memory");
-        }
-      }
-      float4 v[kRowUnroll];
-#pragma unroll
-      for (int u = 0; u < kRowUnroll; ++u) {
-        const int e = e0 + u;
-        v[u] = e < end ? ld4h(base + (int64_t)st.col[e] * w, keep) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      if (weighted) {
-#pragma unroll
-        for (int u = 0; u < kRowUnroll; ++u)
-          if (e0 + u < end) fma4(acc, st.wt[e0 + u], v[u]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < kRowUnroll; ++u) {
-          acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
-        }
-      }
-    }
-  } else {
-    const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
-    for (int64_t e = beg; e < end; ++e) {
-      const int c = __ldg(a.col + e);
-      float wv = a.val != nullptr ? __ldg(a.val + e) : 1.0f;
-      if (SCALED) wv *= __ldg(a.scale + c);
-      fma4(acc, wv, ld4(base + (int64_t)c * w));
-    }
-  }
-  return acc;
-}
-
-// One edge block of a general step of the persistent batched kernel (row-parallel: the LPR
-// lanes of a slot own a row): V_{j+1} = -2 vs^2 (sum_e w_e V_j[col_e]) - V_{j-1},
-// Psi += a_{j+1} T_{j+1}; partials <T_{j+1},T_{j+1}>, <T_{j+1},T_j> accumulated into acc (first
-// lane of each slot).
-template <int LPR, typename TP, typename ST>
-__device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, double (&acc)[2]) {
-  constexpr int S = 32 / LPR;
-  constexpr int kRowsPerPass = (kBlock / 32) * S;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int slot = lane / LPR, sub = lane % LPR;
-  const float* __restrict__ tg = static_cast<const float*>(a.tg);
-  const TP* __restrict__ tp = static_cast<const TP*>(a.tp);
-  const int w = a.w;
-  const float aj = a.psi != nullptr ? __ldg(a.coef + a.j + 1) : 0.f;
-  int rs, re;
-  bool staged;
-  __syncthreads();
-  staged = stage_block<false>(a, st, b, rs, re);
-  __syncthreads();
-  for (int r0 = rs; r0 < re; r0 += kRowsPerPass) {
-    const int r = r0 + wid * S + slot;
-    const bool valid = r < re;
-    const int64_t row = valid ? r : rs;
-    // own-row operands are independent of the gather: issue them first
-    float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), own = prev, p = prev;
-    float vsi = 1.f, ivsi = 1.f;
-    const uint64_t stream = l2_stream();
-    if (valid) {
-      vsi = __ldg(a.vs + row);
-      ivsi = __ldg(a.ivs + row);
-      prev = ld4h(tp + row * w + sub * 4, stream);
-      own = ld4h(tg + row * w + sub * 4, l2_keep());
-      if (a.psi != nullptr) p = ld4h(a.psi + row * a.ldp + sub * 4, stream);
-    }
-    const float4 g = gather_own_row<LPR>(a, st, staged, tg, row, r - rs, valid, sub);
-    float e = 0.f, f = 0.f;
-    if (valid) {
-      const float c2 = -2.0f * vsi * vsi;
-      if (a.tp_unscaled) { prev.x *= vsi; prev.y *= vsi; prev.z *= vsi; prev.w *= vsi; }
-      float4 v;
-      v.x = fmaf(c2, g.x, -prev.x);
-      v.y = fmaf(c2, g.y, -prev.y);
-      v.z = fmaf(c2, g.z, -prev.z);
-      v.w = fmaf(c2, g.w, -prev.w);
-      st4(a.tn + row * w + sub * 4, v);
-      const float4 t = make_float4(v.x * ivsi, v.y * ivsi, v.z * ivsi, v.w * ivsi);
-      const float4 tc = make_float4(own.x * ivsi, own.y * ivsi, own.z * ivsi, own.w * ivsi);
-      if (a.psi != nullptr) {
-        p.x = fmaf(aj, t.x, p.x);
-        p.y = fmaf(aj, t.y, p.y);
-        p.z = fmaf(aj, t.z, p.z);
-        p.w = fmaf(aj, t.w, p.w);
-        st4h(a.psi + row * a.ldp + sub * 4, p, stream);
-      }
-      e = dot4(t, t);
-      f = dot4(t, tc);
-    }
-#pragma unroll
-    for (int off = 1; off < LPR; off <<= 1) {
-      e += __shfl_xor_sync(kFull, e, off);
-      f += __shfl_xor_sync(kFull, f, off);
-    }
-    if (sub == 0 && valid) {
-      acc[0] += (double)e;
-      acc[1] += (double)f;
-    }
   }
 }
 
@@ -409,6 +136,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, ST& st, int b, dou
 constexpr int kChunkRows = kBlock - 1;  // at most one row offset per thread
 constexpr int kChunkEdges = 5632;       // staged columns and weights: 45 KB
 constexpr int kEdgesPerSlot = 64;       // spr: smallest power of two with spr * 64 >= max degree
+constexpr int kRowUnroll = 8;           // 16-byte gathers in flight per lane
 
 struct StageChunk {
   union {
@@ -423,6 +151,12 @@ struct StageChunk {
   int maxdeg;
 };
 
+// Loads of gathered and own rows: through L1 (ld.global.nc) in the standalone step kernels, where
+// the blocks are read-only for the launch; at L2 only (ld.global.cg) in the persistent batched
+// kernel, whose blocks are written by other CTAs of the same launch.
+template <bool CG, typename T>
+__device__ __forceinline__ float4 ldr(const T* ptr);
+
 // Gathered-row loads through L1 (ld.global.nc).
 __device__ __forceinline__ float4 ldg_row(const float* ptr) { return __ldg(reinterpret_cast<const float4*>(ptr)); }
 __device__ __forceinline__ float4 ldg_row(const __nv_bfloat16* ptr) {
@@ -430,6 +164,12 @@ __device__ __forceinline__ float4 ldg_row(const __nv_bfloat16* ptr) {
   const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
   const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
   return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+template <bool CG, typename T>
+__device__ __forceinline__ float4 ldr(const T* ptr) {
+  if constexpr (CG) return ld4(ptr);
+  else return ldg_row(ptr);
 }
 
 // Stages the longest run of rows [r, r + rows) of a block ending at re whose edges fit the
@@ -533,25 +273,25 @@ __device__ __forceinline__ void row_epilogue(const StepArgs& a, int64_t row, int
 }
 
 // Own-row operands of a row, issued before its gather.
-template <bool FIRST, typename TG, typename TP>
+template <bool FIRST, typename TG, typename TP, bool CG = false>
 __device__ __forceinline__ void row_operands(const StepArgs& a, int64_t row, int sub, float4& own,
                                              float4& prev, float4& p, float& sc, float& vsi, float& ivsi) {
   const uint64_t stream = l2_stream();
   const int w = a.w;
   vsi = __ldg(a.vs + row);
   if constexpr (FIRST) {
-    own = ldg_row(static_cast<const TG*>(a.tg) + row * w + sub * 4);
+    own = ldr<CG>(static_cast<const TG*>(a.tg) + row * w + sub * 4);
     sc = -__ldg(a.scale + row);
   } else {
     ivsi = __ldg(a.ivs + row);
     prev = ld4h(static_cast<const TP*>(a.tp) + row * w + sub * 4, stream);
-    own = ldg_row(static_cast<const float*>(a.tg) + row * w + sub * 4);
+    own = ldr<CG>(static_cast<const float*>(a.tg) + row * w + sub * 4);
     if (a.psi != nullptr) p = ld4h(a.psi + row * a.ldp + sub * 4, stream);
   }
 }
 
 // Rows [r, r + rows) of a staged chunk; dot partials into acc (lane 0 of each row's lead slot).
-template <int LPR, bool FIRST, typename TG, typename TP>
+template <int LPR, bool FIRST, typename TG, typename TP, bool CG = false>
 __device__ __forceinline__ void process_chunk(const StepArgs& a, const StageChunk& st, int r, int rows,
                                               float c0, float c1, double (&acc)[FIRST ? 3 : 2]) {
   constexpr int S = 32 / LPR;
@@ -574,7 +314,7 @@ __device__ __forceinline__ void process_chunk(const StepArgs& a, const StageChun
     const int64_t row = (int64_t)r + (valid ? rl : 0);
     float4 own = make_float4(0.f, 0.f, 0.f, 0.f), prev = own, p = own;
     float sc = 0.f, vsi = 1.f, ivsi = 1.f;
-    if (lead) row_operands<FIRST, TG, TP>(a, row, sub, own, prev, p, sc, vsi, ivsi);
+    if (lead) row_operands<FIRST, TG, TP, CG>(a, row, sub, own, prev, p, sc, vsi, ivsi);
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
       const int beg = st.rp[rl], end = st.rp[rl + 1];
@@ -594,7 +334,7 @@ __device__ __forceinline__ void process_chunk(const StepArgs& a, const StageChun
 #pragma unroll
         for (int u = 0; u < kRowUnroll; ++u) {
           const int e = e0 + u * spr;
-          v[u] = e < end ? ldg_row(base + (int64_t)st.u.e.col[e] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[u] = e < end ? ldr<CG>(base + (int64_t)st.u.e.col[e] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (scaled) {
 #pragma unroll
@@ -624,7 +364,7 @@ __device__ __forceinline__ void process_chunk(const StepArgs& a, const StageChun
 }
 
 // A row too long to stage, reduced by the whole CTA from global memory.
-template <int LPR, bool FIRST, typename TG, typename TP>
+template <int LPR, bool FIRST, typename TG, typename TP, bool CG = false>
 __device__ __forceinline__ void coop_row(const StepArgs& a, StageChunk& st, int64_t row, float c0, float c1,
                                          double (&acc)[FIRST ? 3 : 2]) {
   constexpr int S = 32 / LPR;
@@ -635,7 +375,7 @@ __device__ __forceinline__ void coop_row(const StepArgs& a, StageChunk& st, int6
   const bool lead = threadIdx.x < LPR;
   float4 own = make_float4(0.f, 0.f, 0.f, 0.f), prev = own, p = own;
   float sc = 0.f, vsi = 1.f, ivsi = 1.f;
-  if (lead) row_operands<FIRST, TG, TP>(a, row, sub, own, prev, p, sc, vsi, ivsi);
+  if (lead) row_operands<FIRST, TG, TP, CG>(a, row, sub, own, prev, p, sc, vsi, ivsi);
   const TG* __restrict__ base = static_cast<const TG*>(a.tg) + sub * 4;
   const int w = a.w;
   const int64_t beg = __ldg(a.row_ptr + row), end = __ldg(a.row_ptr + row + 1);
@@ -656,7 +396,7 @@ __device__ __forceinline__ void coop_row(const StepArgs& a, StageChunk& st, int6
     float4 v[kRowUnroll];
 #pragma unroll
     for (int u = 0; u < kRowUnroll; ++u)
-      v[u] = e0 + (int64_t)u * TS < end ? ldg_row(base + (int64_t)c[u] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[u] = e0 + (int64_t)u * TS < end ? ldr<CG>(base + (int64_t)c[u] * w) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < kRowUnroll; ++u) fma4(g, wt[u], v[u]);
   }
@@ -687,6 +427,22 @@ __device__ __forceinline__ void coop_row(const StepArgs& a, StageChunk& st, int6
   }
 }
 
+// Rows [r, re) in chunks: staged chunks row by row, a row too long to stage by the whole CTA.
+template <int LPR, bool FIRST, typename TG, typename TP, bool CG>
+__device__ __forceinline__ void rows_range(const StepArgs& a, StageChunk& st, int r, int re, float c0, float c1,
+                                           double (&acc)[FIRST ? 3 : 2]) {
+  while (r < re) {
+    const int rows = stage_chunk<FIRST>(a, st, r, re);
+    if (rows == 0) {
+      coop_row<LPR, FIRST, TG, TP, CG>(a, st, r, c0, c1, acc);
+      r += 1;
+    } else {
+      process_chunk<LPR, FIRST, TG, TP, CG>(a, st, r, rows, c0, c1, acc);
+      r += rows;
+    }
+  }
+}
+
 // FIRST: T_1 = L~ T_0 (stored as V_1 = vs T_1), Psi = a_0 T_0 + a_1 T_1, partials <T0,T0>,
 // <T1,T1>, <T1,T0> (TG: storage type of T_0).  Else one general step (TP: storage type of
 // T_{j-1}), partials <T_{j+1},T_{j+1}>, <T_{j+1},T_j>.  Three CTAs per SM (at most 85 registers
@@ -708,20 +464,8 @@ __global__ void __launch_bounds__(kBlock, 3) cheb_rows_kernel(StepArgs a) {
       c1 = __ldg(a.coef + a.j + 1);
     }
   }
-  for (int b = blockIdx.x; b < a.nsblk; b += gridDim.x) {
-    const int re = __ldg(a.srow + b + 1);
-    int r = __ldg(a.srow + b);
-    while (r < re) {
-      const int rows = stage_chunk<FIRST>(a, st, r, re);
-      if (rows == 0) {
-        coop_row<LPR, FIRST, TG, TP>(a, st, r, c0, c1, acc);
-        r += 1;
-      } else {
-        process_chunk<LPR, FIRST, TG, TP>(a, st, r, rows, c0, c1, acc);
-        r += rows;
-      }
-    }
-  }
+  for (int b = blockIdx.x; b < a.nsblk; b += gridDim.x)
+    rows_range<LPR, FIRST, TG, TP, false>(a, st, __ldg(a.srow + b), __ldg(a.srow + b + 1), c0, c1, acc);
   // every lane may hold a partial: reduce the warp first
 #pragma unroll
   for (int k = 0; k < NQ; ++k)
@@ -755,8 +499,8 @@ __device__ __forceinline__ void block_atomic(double (&acc)[NQ], double* dst) {
 
 template <int LPR>
 __device__ void batched_signals(const BatchTile& t, int b) {
-  if (b >= t.a.nblk) return;
-  const int rs = __ldg(t.a.blk_row + b), re = __ldg(t.a.blk_row + b + 1);
+  if (b >= t.a.nsblk) return;
+  const int rs = __ldg(t.a.srow + b), re = __ldg(t.a.srow + b + 1);
   const int w = t.a.w;
   const uint32_t k0 = (uint32_t)t.seed, k1 = (uint32_t)(t.seed >> 32);
   for (int e = threadIdx.x; e < (re - rs) * w; e += blockDim.x) {
@@ -771,25 +515,25 @@ __device__ void batched_signals(const BatchTile& t, int b) {
   }
 }
 
-struct BatchSmem {
-  Stage e;  // edge-block staging (every step of the persistent kernel)
-};
-
+// One item of the persistent batched kernel: row block b of a tile at step s (s = 1: the first
+// step), through the same chunked rows as the standalone step kernels, with coherent (L2) loads:
+// the blocks a step gathers were written by other CTAs of the same launch.
 template <int LPR>
-__device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
+__device__ void batched_item(const BatchTile& t, StageChunk& st, int b, int s) {
   StepArgs a = t.a;
+  if (b >= a.nsblk) return;
+  const int rs = __ldg(a.srow + b), re = __ldg(a.srow + b + 1);
   if (s == 1) {
-    if (b >= a.nblk) return;
     a.tg = t.buf[0];
     a.tn = static_cast<float*>(t.buf[1]);
     a.j = 0;
     double acc[3] = {0.0, 0.0, 0.0};
-    if (t.t0_dtype == CSC_BF16) first_block<LPR, __nv_bfloat16>(a, sm.e, b, acc);
-    else first_block<LPR, float>(a, sm.e, b, acc);
+    const float c0 = a.psi != nullptr ? __ldg(a.coef) : 0.f, c1 = a.psi != nullptr ? __ldg(a.coef + 1) : 0.f;
+    if (t.t0_dtype == CSC_BF16) rows_range<LPR, true, __nv_bfloat16, float, true>(a, st, rs, re, c0, c1, acc);
+    else rows_range<LPR, true, float, float, true>(a, st, rs, re, c0, c1, acc);
     // first-step rows of the E/F table: E0, E1, F1
     block_atomic<3>(acc, t.mom);
   } else {
-    if (b >= a.nblk) return;
     const int j = s - 1;  // produces T_{j+1}
     a.tg = t.buf[j % 3];
     a.tp = t.buf[(j - 1) % 3];
@@ -797,8 +541,11 @@ __device__ void batched_item(const BatchTile& t, BatchSmem& sm, int b, int s) {
     a.j = j;
     a.tp_unscaled = j == 1;
     double acc[2] = {0.0, 0.0};
-    if (j == 1 && t.t0_dtype == CSC_BF16) step_block<LPR, __nv_bfloat16>(a, sm.e, b, acc);
-    else step_block<LPR, float>(a, sm.e, b, acc);
+    const float c1 = a.psi != nullptr ? __ldg(a.coef + j + 1) : 0.f;
+    if (j == 1 && t.t0_dtype == CSC_BF16)
+      rows_range<LPR, false, float, __nv_bfloat16, true>(a, st, rs, re, 0.f, c1, acc);
+    else
+      rows_range<LPR, false, float, float, true>(a, st, rs, re, 0.f, c1, acc);
     block_atomic<2>(acc, t.mom + 2 * (j + 1) - 1);
   }
 }
@@ -817,7 +564,7 @@ __global__ void __launch_bounds__(kBlock, 3) cheb_batched_kernel(const BatchTile
                                                                  int nwaves, int m,
                                                                  unsigned long long* work,
                                                                  unsigned int* done, int* err) {
-  __shared__ BatchSmem st;
+  __shared__ StageChunk st;
   __shared__ int64_t claim;
   __shared__ int ready;
   const int64_t total = claim_end[nwaves - 1];
@@ -841,7 +588,7 @@ __global__ void __launch_bounds__(kBlock, 3) cheb_batched_kernel(const BatchTile
         volatile unsigned int* dep = done + (size_t)ti * (m + 1) + (s - 1);
         long long spins = 0;
         int ok = 1;
-        while (*dep < (unsigned int)t.a.nblk) {
+        while (*dep < (unsigned int)t.a.nsblk) {
           if (++spins > (1ll << 23) || *(volatile int*)err != 0) {
             atomicExch(err, 1);
             ok = 0;
@@ -864,7 +611,6 @@ __global__ void __launch_bounds__(kBlock, 3) cheb_batched_kernel(const BatchTile
       }
     } else {
       switch (t.lpr) {
-        case 2: batched_item<2>(t, st, b, s); break;
         case 4: batched_item<4>(t, st, b, s); break;
         case 8: batched_item<8>(t, st, b, s); break;
         default: batched_item<16>(t, st, b, s); break;

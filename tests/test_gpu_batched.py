@@ -101,7 +101,7 @@ def test_batched_replay_and_per_graph_agreement(gpu_lib):
 
 def test_batched_weighted_edgeless_tiny_and_several_waves(gpu_lib):
     """A weighted graph, an edgeless graph, a single node, and a 3e5-node graph with 256 columns
-    whose four 64-column tiles each exceed the wave budget (so the schedule crosses waves);
+    whose four 64-column tiles each exceed a 256 MB wave budget (so the schedule crosses waves);
     every graph against the oracle (sampled columns for the large one)."""
     m = 30
     rng = np.random.default_rng(9)
@@ -122,7 +122,7 @@ def test_batched_weighted_edgeless_tiny_and_several_waves(gpu_lib):
                           col_idx=torch.from_numpy(g.col_idx).cuda(),
                           vals=None if vals is None else torch.from_numpy(vals).cuda(),
                           c=c, d=c, lambda_c=lam, seed=77 + i, psi=torch.zeros((g.n, c), device="cuda")))
-    with gpu_lib.Context() as ctx:
+    with gpu_lib.Context({"wave_bytes": 256 << 20}) as ctx:
         mu = ctx.filter_batched(descs, m)
         st = ctx.stats()
     assert st["batched_waves"] >= 4
