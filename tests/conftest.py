@@ -34,10 +34,8 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def fp32_floor(lt, r, a, ref):
-    """Error against ``ref`` of a plain float32 evaluation of sum_j a_j T_j(L~) R by the
-    three-term recursion: the rounding floor that any float32 implementation of the filter
-    meets at this size (large when the output cancels, e.g. h(1) on an edgeless graph)."""
+def fp32_filter(lt, r, a):
+    """A plain float32 evaluation of sum_j a_j T_j(L~) R by the three-term recursion."""
     lt32 = lt.astype(np.float32)
     a32 = np.asarray(a, dtype=np.float32)
     t_prev = np.asarray(r, dtype=np.float32)
@@ -46,7 +44,14 @@ def fp32_floor(lt, r, a, ref):
     for j in range(2, a32.size):
         t_prev, t_cur = t_cur, 2.0 * (lt32 @ t_cur) - t_prev
         out += a32[j] * t_cur
-    return rel(out, ref)
+    return out
+
+
+def fp32_floor(lt, r, a, ref):
+    """Error against ``ref`` of a plain float32 evaluation of sum_j a_j T_j(L~) R by the
+    three-term recursion: the rounding floor that any float32 implementation of the filter
+    meets at this size (large when the output cancels, e.g. h(1) on an edgeless graph)."""
+    return rel(fp32_filter(lt, r, a), ref)
 
 
 def graph_from_edges(n, edges):
