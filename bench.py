@@ -549,7 +549,8 @@ def sbm_extra(a, rank, dist, clocks_cls, local):
             "roofline": roofline(stats, SBM["n"], nnz_mean, int(stats["tile"]), SBM["name"]),
             "kmeans_iters": [i["iters"] for i in info],
             "kmeans": {"passes": stats["kmeans_passes"],
-                       "near_ties_per_pass": stats["kmeans_near_ties"] / max(1, stats["kmeans_passes"])},
+                       "near_ties_per_pass": stats["kmeans_near_ties"] / max(1, stats["kmeans_passes"]),
+                       "rows_evaluated_fraction": stats["kmeans_rows"] / max(1, stats["kmeans_passes"] * SBM["n"])},
             "compressive_kmeans": comp}
 
 
@@ -631,7 +632,8 @@ def run_ours(a, rank, world, local):
                      "evals": [i["evals"] for i in info], "kmeans_iters": [i["iters"] for i in info],
                      "filter_ms": [i["filter_ms"] for i in info], "cluster_ms": [i["cluster_ms"] for i in info]},
         "kmeans": {"passes": stats["kmeans_passes"],
-                   "near_ties_per_pass": stats["kmeans_near_ties"] / max(1, stats["kmeans_passes"])},
+                   "near_ties_per_pass": stats["kmeans_near_ties"] / max(1, stats["kmeans_passes"]),
+                   "rows_evaluated_fraction": stats["kmeans_rows"] / max(1, stats["kmeans_passes"] * n)},
         "nnz_mean": nnz_timed,
         "sbm_1e6": sbm,
         "batched_vs_plain": batched,

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 7
+#define CSC_ABI_VERSION 8
 
 typedef struct csc_ctx csc_ctx;
 
@@ -109,6 +109,9 @@ typedef struct csc_stats {
                                tile of width w, 4 nnz (col_idx; 8 nnz when weighted) + 8 (n+1)
                                (row_ptr) + 4 n (D^-1/2) + n w (s + 4 + 4 + 8) (V_{j-1} of s bytes
                                per value, V_j, V_{j+1}, Psi read and write) */
+  int64_t kmeans_rows;      /* rows whose distances a k-means pass evaluated, summed over passes
+                               (every row in the first pass of a call; later passes skip the rows
+                               whose Hamerly bounds certify their centroid) */
 } csc_stats;
 
 /* ---------------------------------------------------------------- library */

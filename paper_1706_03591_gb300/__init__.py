@@ -129,7 +129,8 @@ def csc_get_stats(h, reset: bool = False) -> dict:
                 filter_passes=st.filter_passes, tile=st.tile, batched_launches=st.batched_launches,
                 graph_replays=st.graph_replays, autotune_trials=st.autotune_trials,
                 batched_waves=st.batched_waves, kmeans_passes=st.kmeans_passes,
-                kmeans_near_ties=st.kmeans_near_ties, step_bytes=st.step_bytes)
+                kmeans_near_ties=st.kmeans_near_ties, step_bytes=st.step_bytes,
+                kmeans_rows=st.kmeans_rows)
 
 
 def csc_set_graph(h, n: int, row_ptr, col_idx, vals=None) -> None:

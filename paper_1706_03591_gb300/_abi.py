@@ -44,6 +44,7 @@ class csc_stats(C.Structure):
         ("kmeans_passes", C.c_int64),
         ("kmeans_near_ties", C.c_int64),
         ("step_bytes", C.c_double),
+        ("kmeans_rows", C.c_int64),
     ]
 
 

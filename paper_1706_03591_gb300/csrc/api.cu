@@ -596,11 +596,12 @@ csc_status csc_get_stats(csc_ctx* ctx, csc_stats* out, int reset) {
   out->batched_waves = ctx->batched_waves;
   out->kmeans_passes = ctx->kmeans_passes;
   out->kmeans_near_ties = ctx->kmeans_near_ties;
+  out->kmeans_rows = ctx->kmeans_rows;
   out->step_bytes = ctx->step_bytes;
   if (reset) {
     ctx->launches = ctx->step_launches = ctx->filter_passes = 0;
     ctx->batched_launches = ctx->graph_replays = ctx->autotune_trials = 0;
-    ctx->kmeans_passes = ctx->kmeans_near_ties = 0;
+    ctx->kmeans_passes = ctx->kmeans_near_ties = ctx->kmeans_rows = 0;
     ctx->step_ms = 0.0;
     ctx->step_bytes = 0.0;
   }
@@ -1121,6 +1122,7 @@ csc_status csc_kmeans(csc_ctx* ctx, const void* Y, int y_dtype, int64_t n, int d
   ctx->launches += res.launches;
   ctx->kmeans_passes += res.iters;
   ctx->kmeans_near_ties += res.near_ties;
+  ctx->kmeans_rows += res.decided;
   if (st != CSC_OK) return st;
   const cudaMemcpyKind kind = assign_where == CSC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   CUDA_OK(cudaMemcpyAsync(assign_out, res.assign, (size_t)n * 4, kind, s));
@@ -1161,6 +1163,7 @@ csc_status csc_cluster(csc_ctx* ctx, int k, uint64_t seed, const int64_t* init_i
   ctx->launches += res.launches;
   ctx->kmeans_passes += res.iters;
   ctx->kmeans_near_ties += res.near_ties;
+  ctx->kmeans_rows += res.decided;
   if (st != CSC_OK) return st;
   ALLOC_OK(csc::ensure(ctx->prev_assign, (size_t)n * 4));
   CUDA_OK(cudaMemcpyAsync(ctx->prev_assign.ptr, res.assign, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
@@ -1269,6 +1272,7 @@ csc_status csc_compressive_cluster(csc_ctx* ctx, const float* theta, const void*
     ctx->launches += res.launches;
     ctx->kmeans_passes += res.iters;
     ctx->kmeans_near_ties += res.near_ties;
+    ctx->kmeans_rows += res.decided;
     if (st != CSC_OK) return st;
     inertia[r] = res.inertia;
     CUDA_OK(cudaMemcpyAsync(csc::as<int32_t>(cs.labels) + (size_t)r * n_omega, res.assign, (size_t)n_omega * 4,

@@ -29,6 +29,33 @@ void release(DevBuf& b);
 template <typename T>
 inline T* as(DevBuf& b) { return static_cast<T*>(b.ptr); }
 
+#ifdef __CUDACC__
+// Eight consecutive feature values as float through the read-only path: one 16-byte load of
+// bfloat16, two of float32.  p must be 16-byte aligned.
+__device__ __forceinline__ void ld8(const __nv_bfloat16* p, float (&v)[8]) {
+  const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+#endif
+
+// Whether rows of features can be read eight values at a time (ld8): d and the leading
+// dimension multiples of 8, base 16-byte aligned.
+inline bool rows_vec8(const void* y, int64_t d, int64_t ldy) {
+  return d % 8 == 0 && ldy % 8 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
+}
+
 // ------------------------------------------------------------------ graph state
 
 struct Graph {
@@ -266,7 +293,12 @@ struct KmeansState {
   DevBuf ysplit, ynorm;         // bfloat16 [1 or 2][dp / 64][n][64] (y0, y1), float2 [n] row norms
   DevBuf csplit, cn2t;          // bfloat16 [2][npad][dp] (c0, c1), float [npad] |c|^2
   DevBuf masks;                 // uint16 [n][npad / 16] candidate masks of near-tie rows
-  alignas(64) unsigned char tmaps[3][128];  // TMA maps of y0, y1 and (c0, c1)
+  DevBuf y2b;                   // float2 [n]: |y|^2 rounded down and up
+  DevBuf bnd;                   // float2 [n]: Hamerly bounds (upper to the own centroid, lower to the others)
+  DevBuf hsel;                  // int32 [n]: rows whose bounds do not certify their centroid
+  DevBuf ycomp;                 // bfloat16, the layout of ysplit: those rows, compacted
+  bool tc_rowmajor = false;     // bfloat16 features read in place by the distance pass (no ysplit)
+  alignas(64) unsigned char tmaps[5][128];  // TMA maps of y0, y1, (c0, c1), compacted y0, y1
   unsigned long long* hist_host = nullptr;   // pinned [passes][5]: counters of each pass
   size_t hist_cap = 0;
   cudaEvent_t pass_ev[2] = {nullptr, nullptr};  // completion of a pass's counter copy
@@ -287,9 +319,13 @@ TcPlan kmeans_tc_plan(int64_t n, int k, int d, int y_dtype);
 cudaError_t kmeans_tc_prepare(KmeansState& st, const TcPlan& p, const void* y, int y_dtype, int64_t n,
                               int d, int64_t ldy, unsigned int* maxabs_bits, cudaStream_t s);
 // One assignment pass against the float64 centroids in st.c64: counters[0] moves (recorded in
-// st.moved when track), counters[1] near-tie rows, counters[4] error word (a wait expired).
+// st.moved when track), counters[1] near-tie rows, counters[2] rows the pass evaluated (when
+// select), counters[4] error word (a wait expired).  Every evaluated row leaves Hamerly bounds
+// in st.bnd.  select: rows whose bounds, moved by the centroid drift of the last update
+// (st.cmove), certify their centroid are skipped; the pass evaluates the others (compacted
+// when they are at most a fifth of the rows, else all rows).
 cudaError_t kmeans_tc_pass(KmeansState& st, const TcPlan& p, const void* y, int y_dtype, int64_t n, int d,
-                           int64_t ldy, int k, int track, cudaStream_t s);
+                           int64_t ldy, int k, int track, bool select, cudaStream_t s);
 void kmeans_tc_release(KmeansState& st);
 
 struct KmeansResult {
@@ -369,6 +405,6 @@ struct csc_ctx {
   std::vector<uint64_t> b_sig;              // launch signature of b_exec
   std::map<uint64_t, int> tune;             // size class -> column tile
   int64_t batched_launches = 0, graph_replays = 0, autotune_trials = 0, batched_waves = 0;
-  int64_t kmeans_passes = 0, kmeans_near_ties = 0;
+  int64_t kmeans_passes = 0, kmeans_near_ties = 0, kmeans_rows = 0;
 };
 

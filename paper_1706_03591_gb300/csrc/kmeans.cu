@@ -39,6 +39,48 @@ constexpr int kAssignBlock = 256;
 __device__ __forceinline__ float ldf(const float* p) { return *p; }
 __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
+// Fixed-point value of a feature: x = y * 2^S (exact in float) rounded to the nearest integer,
+// ties to even, from the float's fields with integer operations (the float-to-int64 conversion
+// instruction runs on the FP64 pipe, which this part has little of).  Finite x, |x| < 2^63.
+__device__ __forceinline__ long long fixed_rn(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xFFu);
+  const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;  // x = m 2^(e - 150) for e >= 1
+  long long q;
+  if (e >= 150) {
+    q = (long long)m << (e - 150);
+  } else if (e < 126) {
+    q = 0;  // |x| < 1/2
+  } else {
+    const int sh = 150 - e;  // 1 .. 24
+    const uint32_t qi = m >> sh, r = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    q = (long long)(qi + ((r > half || (r == half && (qi & 1u))) ? 1u : 0u));
+  }
+  return (b >> 31) ? -q : q;
+}
+
+// fixed_rn(y * 2^S) of a bfloat16 feature from its bits h: y = m 2^(e - 134), so the value is
+// m shifted by e - 134 + S, rounded to nearest, ties to even, when the shift is negative.
+// Equal to fixed_rn(float(y) * 2^S) (the same real number, the same rounding).
+__device__ __forceinline__ long long fixed_bf16(uint32_t h, int S) {
+  const int e = (int)((h >> 7) & 0xFFu);
+  const uint32_t m = (h & 0x7Fu) | 0x80u;
+  const int sh = e - 134 + S;
+  long long q;
+  if (e == 0) {
+    q = 0;  // zero or subnormal: |y| 2^S < 2^(S - 126) < 1/2
+  } else if (sh >= 0) {
+    q = (long long)m << sh;
+  } else if (sh < -8) {
+    q = 0;  // m 2^sh < 2^(8 + sh) <= 1/2 exclusive
+  } else {
+    const int r = -sh;  // 1 .. 8
+    const uint32_t qi = m >> r, rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
+    q = (long long)(qi + ((rem > half || (rem == half && (qi & 1u))) ? 1u : 0u));
+  }
+  return (h & 0x8000u) ? -q : q;
+}
+
 template <typename TY>
 __global__ void maxabs_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d,
                               unsigned int* out) {
@@ -94,7 +136,7 @@ __global__ void update_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, 
   for (int64_t row = warp; row < n; row += nwarps) {
     const int a = assign[row];
     for (int l = lane; l < d; l += 32) {
-      const long long q = __float2ll_rn(ldf(y + row * ldy + l) * scale);
+      const long long q = fixed_rn(ldf(y + row * ldy + l) * scale);
       atomicAdd(tsum + (size_t)a * d + l, (unsigned long long)q);
     }
     if (lane == 0) atomicAdd(tcnt + a, 1);
@@ -194,7 +236,7 @@ __global__ void seg_sum_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n,
 #pragma unroll
       for (int i = 0; i < DW; ++i) {
         const int l = lane + 32 * i;
-        if (l < d) acc[i] += __float2ll_rn(ldf(y + row * ldy + l) * scale);
+        if (l < d) acc[i] += fixed_rn(ldf(y + row * ldy + l) * scale);
       }
     }
 #pragma unroll
@@ -202,6 +244,92 @@ __global__ void seg_sum_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n,
       const int l = lane + 32 * i;
       if (l < d && acc[i] != 0) atomicAdd(sums + (size_t)cur * d + l, (unsigned long long)acc[i]);
     }
+  }
+}
+
+// The same sums with eight values per lane (rows read with 16-byte loads) over runs of C
+// bucketed rows, C chosen so that each warp of the grid takes about one run.  The cluster of
+// bucket slot p follows from the bucket starts (prefix sums of counts, in shared memory), so a
+// row costs one dependent load: the warp reads 32 slots of perm at once and keeps U rows in
+// flight.  d <= 256, k <= 1024, rows_vec8.  The per-element fixed-point values and therefore
+// the integer sums are those of seg_sum_kernel.
+template <typename TY>
+__global__ void seg_sum_vec_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d,
+                                   const int32_t* __restrict__ perm, const int* __restrict__ counts, int k,
+                                   float scale, int S, unsigned long long* __restrict__ sums, int64_t C) {
+  constexpr int U = 8;
+  constexpr bool kBf16 = sizeof(TY) == 2;  // bfloat16 rows: fixed point from the bits (fixed_bf16)
+  __shared__ long long start[1025];
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int j = 0; j < k; ++j) { start[j] = acc; acc += counts[j]; }
+    start[k] = acc;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const bool act = 8 * lane < d;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c0 = warp * C; c0 < n; c0 += nwarps * C) {
+    const int64_t c1 = min(n, c0 + C);
+    // cluster of slot c0: the last j with start[j] <= c0
+    int lo = 0, hi = k - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= c0) lo = mid; else hi = mid - 1;
+    }
+    int cur = lo;
+    long long next = start[cur + 1];
+    long long acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0;
+    for (int64_t p32 = c0; p32 < c1; p32 += 32) {
+      const int32_t pv = p32 + lane < c1 ? perm[p32 + lane] : 0;
+      const int cnt = (int)min((int64_t)32, c1 - p32);
+      for (int b = 0; b < cnt; b += U) {
+        float v[U][8];
+        uint4 raw[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t row = __shfl_sync(0xffffffffu, pv, (b + u) & 31);
+          if constexpr (kBf16) {
+            raw[u] = (b + u < cnt && act) ? __ldg(reinterpret_cast<const uint4*>(y + row * ldy + 8 * lane))
+                                          : make_uint4(0u, 0u, 0u, 0u);
+          } else if (b + u < cnt && act) {
+            ld8(y + row * ldy + 8 * lane, v[u]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[u][e] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (b + u >= cnt) break;
+          const int64_t p = p32 + b + u;
+          if (p >= next) {
+            if (act)
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                if (acc[e] != 0) atomicAdd(sums + (size_t)cur * d + 8 * lane + e, (unsigned long long)acc[e]);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[e] = 0;
+            while (p >= next) next = start[++cur + 1];
+          }
+          if constexpr (kBf16) {
+            const uint32_t w[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[e] += fixed_bf16((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu, S);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[e] += fixed_rn(v[u][e] * scale);
+          }
+        }
+      }
+    }
+    if (act)
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (acc[e] != 0) atomicAdd(sums + (size_t)cur * d + 8 * lane + e, (unsigned long long)acc[e]);
   }
 }
 
@@ -796,7 +924,7 @@ __global__ void move_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, in
     const int64_t row = moved[m];
     const int old = moved[n + m], nw = moved[2 * n + m];
     for (int l = lane; l < d; l += 32) {
-      const long long q = __float2ll_rn(ldf(y + row * ldy + l) * scale);
+      const long long q = fixed_rn(ldf(y + row * ldy + l) * scale);
       atomicAdd(sums + (size_t)nw * d + l, (unsigned long long)q);
       atomicAdd(sums + (size_t)old * d + l, (unsigned long long)(-q));
     }
@@ -832,6 +960,63 @@ __global__ void inertia_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n,
     double s = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
     part[blockIdx.x] = s;
+  }
+}
+
+// The same inertia with eight values per lane (rows_vec8): each warp takes a contiguous run
+// of rows, reads their labels 32 at a time, keeps U rows in flight, and sums its lanes' float
+// partials in float64, reduced once at the end.
+template <typename TY>
+__global__ void inertia_vec_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d,
+                                   const float* __restrict__ c32, const int32_t* __restrict__ assign,
+                                   double* __restrict__ part) {
+  constexpr int U = 4;
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int groups = d / 8;
+  const int64_t C = (n + nwarps - 1) / nwarps;
+  const int64_t r0 = warp * C, r1 = min(n, r0 + C);
+  double acc = 0.0;
+  for (int64_t p32 = r0; p32 < r1; p32 += 32) {
+    const int av = p32 + lane < r1 ? assign[p32 + lane] : 0;
+    const int cnt = (int)min((int64_t)32, r1 - p32);
+    for (int b = 0; b < cnt; b += U) {
+      int a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] = __shfl_sync(0xffffffffu, av, (b + u) & 31);
+      float s = 0.f;
+      for (int g = lane; g < groups; g += 32) {
+        float v[U][8], q[U][8];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (b + u < cnt) {
+            ld8(y + (p32 + b + u) * ldy + 8 * g, v[u]);
+            ld8(c32 + (size_t)a[u] * d + 8 * g, q[u]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[u][e] = q[u][e] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float df = v[u][e] - q[u][e];
+            s = fmaf(df, df, s);
+          }
+      }
+      acc += (double)s;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    part[blockIdx.x] = t;
   }
 }
 
@@ -896,6 +1081,7 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
                      cudaStream_t s, KmeansResult* res, std::string* err) {
   const size_t kd = (size_t)k * d;
   const int sms = num_sms();
+  const bool vec8 = rows_vec8(y, d, ldy);  // rows read with 16-byte loads
   const int y_dtype = sizeof(TY) == 2 ? CSC_BF16 : CSC_F32;
   const TcPlan tp = kmeans_tc_plan(n, k, d, y_dtype);
   const bool use_tc = tp.ok;
@@ -981,7 +1167,10 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
       sort_scatter_kernel<<<sort_grid, kSortBlock, (size_t)k * 4, s>>>(asg, n, k, hist, perm);
       const int g = sms * 8;
       unsigned long long* sums = as<unsigned long long>(st.sums);
-      if (d <= 32)
+      if (vec8)
+        seg_sum_vec_kernel<TY><<<g, 256, 0, s>>>(y, ldy, n, d, perm, as<int>(st.counts), k, scale, S, sums,
+                                                 std::max<int64_t>(64, (n + (int64_t)g * 8 - 1) / ((int64_t)g * 8)));
+      else if (d <= 32)
         seg_sum_kernel<TY, 1><<<g, 256, 0, s>>>(y, ldy, n, d, perm, asg, scale, sums);
       else if (d <= 64)
         seg_sum_kernel<TY, 2><<<g, 256, 0, s>>>(y, ldy, n, d, perm, asg, scale, sums);
@@ -1020,7 +1209,8 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   CK(finalize());
 
   if (use_tc) {
-    // Tensor-core distance pass on every row each pass; near ties decided in float64.  The
+    // Tensor-core distance pass (every row in the first pass; later passes skip the rows whose
+    // Hamerly bounds certify their centroid); near ties decided in float64.  The
     // host queues pass it before it reads the counters of pass it - 1 (copied to pinned
     // memory), so the GPU does not wait for the host between passes.  The update after pass
     // it is either the full recomputation or the incremental one from the moved rows; both
@@ -1040,6 +1230,12 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     CK(cudaMemsetAsync(counters + 4, 0, 8, s));
     int examined = 0, stop = 0;
     unsigned long long last_moved = ~0ull;
+    // bound selection per pass; it stops while it does not pay (the last examined selecting pass
+    // evaluated every row in place) and is tried again every kSelectRetry passes
+    constexpr int kSelectRetry = 4;
+    std::vector<char> selected((size_t)max_iter + 2, 0);
+    bool select_paid = true;
+    int last_select = 0;
     bool converged = false;
     int64_t decided = 0;
     // reads the counters of pass j (1-based) once its copy has completed
@@ -1056,9 +1252,11 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
         return CSC_ETIMEOUT;
       }
       res->near_ties += (int64_t)cnt[1];
-      decided += n;
+      decided += selected[j] ? (int64_t)cnt[2] : n;  // a selecting pass evaluates cnt[2] rows
+      if (selected[j]) select_paid = cnt[2] < (unsigned long long)n;
       examined = j;
-      last_moved = j == 1 ? ~0ull : cnt[0];  // the first pass does not record moves
+      // a cold first pass does not record moves; a warm one records them against prev_assign
+      last_moved = (j == 1 && prev_assign == nullptr) ? ~0ull : cnt[0];
       if (debug_on()) {
         fprintf(stderr, "[csc] kmeans tc pass %d: near ties %llu moved %llu\n", j, cnt[1], cnt[0]);
         fflush(stderr);
@@ -1069,7 +1267,12 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     for (int it = 1; it <= max_iter; ++it) {
       CK(cudaMemsetAsync(counters, 0, 32, s));
       TRACE("tc pass");
-      CK(kmeans_tc_pass(st, tp, y, y_dtype, n, d, ldy, k, it > 1, s));
+      const bool sel = it > 1 && (select_paid || it - last_select >= kSelectRetry);
+      selected[it] = sel;
+      if (sel) last_select = it;
+      if (it == 1 && prev_assign != nullptr)
+        CK(cudaMemcpyAsync(st.assign.ptr, prev_assign, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+      CK(kmeans_tc_pass(st, tp, y, y_dtype, n, d, ldy, k, it > 1 || prev_assign != nullptr, sel, s));
       launches += 3;
       CK(cudaMemcpyAsync(st.hist_host + (size_t)(it - 1) * 5, counters, 40, cudaMemcpyDeviceToHost, s));
       CK(cudaEventRecord(st.pass_ev[it & 1], s));
@@ -1197,8 +1400,12 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   // inertia against the centroids the final assignment was computed with
   const int igrid = sms * 8;
   TRACE("inertia");
-  inertia_kernel<TY><<<igrid, 256, 0, s>>>(y, ldy, n, d, as<float>(st.c32), as<int32_t>(st.assign),
-                                            as<double>(st.inertia_part));
+  if (vec8)
+    inertia_vec_kernel<TY><<<igrid, 256, 0, s>>>(y, ldy, n, d, as<float>(st.c32), as<int32_t>(st.assign),
+                                                as<double>(st.inertia_part));
+  else
+    inertia_kernel<TY><<<igrid, 256, 0, s>>>(y, ldy, n, d, as<float>(st.c32), as<int32_t>(st.assign),
+                                              as<double>(st.inertia_part));
   CK(cudaGetLastError());
   CK(launch_reduce_partials(as<double>(st.inertia_part), 1, igrid, 1, 0,
                             as<double>(st.inertia_part) + igrid, s));

@@ -29,6 +29,16 @@
 //               streams, and writes the assignment, the moves, or the near-tie candidate mask.
 // Every mbarrier wait is bounded (about a second); a wait that runs out sets the error word,
 // the CTA drains its copies and MMAs in flight, frees its TMEM and returns.
+//
+// Rows that cannot move are skipped (Hamerly's bounds).  A decided row leaves an upper bound
+// u >= |y - c_a| (its own centroid a) and a lower bound l <= min_{j != a} |y - c_j|, from
+// best + E and second - E plus |y|^2 in directed rounding; a near-tie row leaves (inf, 0).
+// After the update the centroids move by at most delta_j (float64 norms rounded up), so by the
+// triangle inequality u + delta_a and l - max_{j != a} delta_j are bounds for the new
+// centroids.  A row with u < l keeps a (every other centroid is strictly farther, so no tie
+// either) and is not evaluated; the others are listed, copied into a compact copy of the split
+// rows (when they are at most a fifth of all rows), and the pass runs over that copy.  Skipping
+// changes no assignment, so the sums, centroids and pass count are those of plain Lloyd.
 #include <cuda.h>
 
 #include <algorithm>
@@ -64,7 +74,12 @@ struct TcArgs {
   int32_t* flagged;                 // [n] rows left for the float64 decision
   uint16_t* masks;                  // [n][npad / 16] candidate masks of those rows
   int32_t* moved;                   // [3][n]: row, old, new
-  unsigned long long* counters;     // [0] moved, [1] flagged, [4] error word
+  unsigned long long* counters;     // [0] moved, [1] flagged, [2] rows evaluated, [4] error word,
+                                    // [6] compacted (with sel)
+  const int32_t* sel;               // rows of the compacted copy (nullptr: every row, in place)
+  int rowmajor;                     // tm_y0 maps the bfloat16 feature rows themselves (2-D)
+  const float2* y2b;                // [n] |y|^2 rounded down and up
+  float2* bnd;                      // [n] Hamerly bounds (u, l)
 };
 
 __device__ __forceinline__ float ldf_any(const float* p) { return *p; }
@@ -123,6 +138,12 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 }
 
 // L2 prefetch of one box (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
 __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
   asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
                    reinterpret_cast<uint64_t>(map)),
@@ -230,7 +251,8 @@ __device__ __forceinline__ void set_error(const TcArgs& a, unsigned long long co
 template <int NV>
 __global__ void __launch_bounds__(kThreads, 1)
     kmeans_tc_kernel(const __grid_constant__ CUtensorMap tm_y0, const __grid_constant__ CUtensorMap tm_y1,
-                     const __grid_constant__ CUtensorMap tm_c, const TcArgs a) {
+                     const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_y0c,
+                     const __grid_constant__ CUtensorMap tm_y1c, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base (128-byte swizzle atoms)
   const uint32_t raw = smem_u32(smem_raw);
@@ -248,7 +270,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* cn2s = reinterpret_cast<float*>(tmem_holder + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ntiles = (a.n + kTM - 1) / kTM;
+  // rows of this pass: all n in place, or the selected rows (compacted, or in place when many)
+  int64_t nr = a.n;
+  bool cmp = false;
+  if (a.sel != nullptr) {
+    nr = (int64_t)a.counters[2];
+    cmp = a.counters[6] != 0;
+  }
+  const int64_t ntiles = (nr + kTM - 1) / kTM;
+  const CUtensorMap* my0 = cmp ? &tm_y0c : &tm_y0;
+  const CUtensorMap* my1 = cmp ? &tm_y1c : &tm_y1;
+  const bool rm = a.rowmajor && !cmp;  // 2-D boxes (x = chunk * 64, y = row), else chunk-major 3-D
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
@@ -292,15 +324,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t tp = blockIdx.x; tp < ntiles && tp < blockIdx.x + (int64_t)kPrefetch * gridDim.x;
            tp += gridDim.x)
         for (int kc = 0; kc < a.nk; ++kc) {
-          tma_prefetch_3d(&tm_y0, 0, (int)(tp * kTM), kc);
-          if (a.has_lo) tma_prefetch_3d(&tm_y1, 0, (int)(tp * kTM), kc);
+          if (rm) {
+            tma_prefetch_2d(my0, kc * kKC, (int)(tp * kTM));
+          } else {
+            tma_prefetch_3d(my0, 0, (int)(tp * kTM), kc);
+            if (a.has_lo) tma_prefetch_3d(my1, 0, (int)(tp * kTM), kc);
+          }
         }
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int64_t tp = t + (int64_t)kPrefetch * gridDim.x;
         if (tp < ntiles)
           for (int kc = 0; kc < a.nk; ++kc) {
-            tma_prefetch_3d(&tm_y0, 0, (int)(tp * kTM), kc);
-            if (a.has_lo) tma_prefetch_3d(&tm_y1, 0, (int)(tp * kTM), kc);
+            if (rm) {
+              tma_prefetch_2d(my0, kc * kKC, (int)(tp * kTM));
+            } else {
+              tma_prefetch_3d(my0, 0, (int)(tp * kTM), kc);
+              if (a.has_lo) tma_prefetch_3d(my1, 0, (int)(tp * kTM), kc);
+            }
           }
         for (int kc = 0; kc < a.nk; ++kc) {
           const uint32_t s = q % S, ph = (q / S) & 1u;
@@ -311,8 +351,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mbar_expect_tx(bar(kFull + s), a.stage_bytes);
           const uint32_t dst = sA + s * a.stage_bytes;
-          tma_load_3d(dst, &tm_y0, 0, (int)(t * kTM), kc, bar(kFull + s));
-          if (a.has_lo) tma_load_3d(dst + kChunkA, &tm_y1, 0, (int)(t * kTM), kc, bar(kFull + s));
+          if (rm) {
+            tma_load_2d(dst, my0, kc * kKC, (int)(t * kTM), bar(kFull + s));
+          } else {
+            tma_load_3d(dst, my0, 0, (int)(t * kTM), kc, bar(kFull + s));
+            if (a.has_lo) tma_load_3d(dst + kChunkA, my1, 0, (int)(t * kTM), kc, bar(kFull + s));
+          }
           ++q;
         }
       }
@@ -382,8 +426,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
-      const int64_t row = t * kTM + rl;
-      const bool valid = row < a.n;
+      const int64_t slot_row = t * kTM + rl;
+      const bool valid = slot_row < nr;
+      const int64_t row = !valid ? 0 : (cmp ? (int64_t)a.sel[slot_row] : slot_row);
       const float2 yr = valid ? a.ynorm[row] : make_float2(0.f, 0.f);
       const float yabs = yr.x + yr.y;  // >= |y|
       const float dot_err = (yr.y + a.kdot * yr.x) * cmax;
@@ -443,6 +488,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(bar(kAccEmpty + acc));
       if (flag) a.flagged[slot] = (int32_t)row;
+      if (valid) {
+        // Hamerly bounds against the float64 centroids: |y - c_j|^2 = e_j + |y|^2 with
+        // |f_j - e_j| <= E; a near-tie row is evaluated again next pass
+        float2 bd = make_float2(INFINITY, 0.f);
+        if (!flag) {
+          const float2 y2 = a.y2b[row];
+          bd.x = __fsqrt_ru(__fadd_ru(__fadd_ru(bst, E), y2.y));
+          const float l2 = __fadd_rd(__fsub_rd(sec, E), y2.x);
+          bd.y = l2 > 0.f ? __fsqrt_rd(l2) : 0.f;
+        }
+        a.bnd[row] = bd;
+      }
       bool mv = false;
       int old = 0;
       if (valid && !flag) {
@@ -562,11 +619,13 @@ __global__ void tc_refine_kernel(const TY* __restrict__ y, int64_t ldy, int d, c
 template <typename TY>
 __global__ void split_rows_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d, int dp,
                                   __nv_bfloat16* __restrict__ y0, __nv_bfloat16* __restrict__ y1,
-                                  float2* __restrict__ ynorm, unsigned int* __restrict__ maxabs_bits) {
+                                  float2* __restrict__ ynorm, float2* __restrict__ y2b,
+                                  unsigned int* __restrict__ maxabs_bits) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float infl = 1.0f + (float)(d + 3) * 1.1920928955078125e-7f;
+  const float defl = 1.0f - (float)(d + 3) * 1.1920928955078125e-7f;
   float mx = 0.f;
   for (int64_t row = warp; row < n; row += nwarps) {
     float s0 = 0.f, s1 = 0.f;
@@ -595,9 +654,136 @@ __global__ void split_rows_kernel(const TY* __restrict__ y, int64_t ldy, int64_t
     if (lane == 0) {
       const float r = y1 != nullptr ? 0.0f : __fadd_ru(__fsqrt_ru(__fmul_ru(s1, infl)), 1e-30f);
       ynorm[row] = make_float2(__fsqrt_ru(__fmul_ru(s0, infl)), r);
+      // |y|^2 is s0 (bfloat16 features are y0 exactly, s1 = 0), within (d + 3) 2^-23 relative
+      y2b[row] = make_float2(__fmul_rd(s0, defl), __fmul_ru(s0, infl));
     }
   }
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if (lane == 0) atomicMax(maxabs_bits, __float_as_uint(mx));
+}
+
+// split_rows_kernel with eight values per lane (16-byte loads and stores) and two rows in
+// flight per warp, for rows_vec8 features; the same values, norms and bounds.  y0 == nullptr:
+// norms and max |y| only (bfloat16 features that the distance pass reads in place).
+template <typename TY>
+__global__ void split_rows_vec_kernel(const TY* __restrict__ y, int64_t ldy, int64_t n, int d, int dp,
+                                      __nv_bfloat16* __restrict__ y0, __nv_bfloat16* __restrict__ y1,
+                                      float2* __restrict__ ynorm, float2* __restrict__ y2b,
+                                      unsigned int* __restrict__ maxabs_bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float infl = 1.0f + (float)(d + 3) * 1.1920928955078125e-7f;
+  const float defl = 1.0f - (float)(d + 3) * 1.1920928955078125e-7f;
+  const int groups = dp / 8;
+  float mx = 0.f;
+  for (int64_t r0 = warp; r0 < n; r0 += 2 * nwarps) {
+    float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f};
+    for (int g = lane; g < groups; g += 32) {
+      const int l = 8 * g;
+      float v[2][8];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t row = r0 + q * nwarps;
+        if (row < n && l < d) {
+          ld8(y + row * ldy + l, v[q]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[q][e] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t row = r0 + q * nwarps;
+        if (row >= n) continue;
+        uint32_t h[4], lo[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float v0 = v[q][2 * i], v1 = v[q][2 * i + 1];
+          const float a0 = fabsf(v0), a1 = fabsf(v1);
+          mx = (a0 <= 3.0e38f && a1 <= 3.0e38f) ? fmaxf(mx, fmaxf(a0, a1)) : INFINITY;  // NaN/inf -> inf
+          const __nv_bfloat162 hb = __floats2bfloat162_rn(v0, v1);
+          const float e0 = v0 - __low2float(hb), e1 = v1 - __high2float(hb);  // exact
+          h[i] = *reinterpret_cast<const uint32_t*>(&hb);
+          const __nv_bfloat162 lb = __floats2bfloat162_rn(e0, e1);
+          lo[i] = *reinterpret_cast<const uint32_t*>(&lb);
+          if (y1 != nullptr) {
+            s0[q] = fmaf(v0, v0, fmaf(v1, v1, s0[q]));
+          } else {
+            const float h0 = __low2float(hb), h1 = __high2float(hb);
+            s0[q] = fmaf(h0, h0, fmaf(h1, h1, s0[q]));
+            s1[q] = fmaf(e0, e0, fmaf(e1, e1, s1[q]));
+          }
+        }
+        const size_t off = ((size_t)(l >> 6) * n + row) * kKC + (l & 63);
+        if (y0 != nullptr) *reinterpret_cast<uint4*>(y0 + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        if (y1 != nullptr) *reinterpret_cast<uint4*>(y1 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      for (int off = 16; off > 0; off >>= 1) {
+        s0[q] += __shfl_xor_sync(0xffffffffu, s0[q], off);
+        s1[q] += __shfl_xor_sync(0xffffffffu, s1[q], off);
+      }
+      const int64_t row = r0 + q * nwarps;
+      if (lane == 0 && row < n) {
+        const float r = y1 != nullptr ? 0.0f : __fadd_ru(__fsqrt_ru(__fmul_ru(s1[q], infl)), 1e-30f);
+        ynorm[row] = make_float2(__fsqrt_ru(__fmul_ru(s0[q], infl)), r);
+        y2b[row] = make_float2(__fmul_rd(s0[q], defl), __fmul_ru(s0[q], infl));
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if (lane == 0) atomicMax(maxabs_bits, __float_as_uint(mx));
+}
+
+// Row norms of bfloat16 features that the distance pass reads in place (rows_vec8, d a multiple
+// of 64): ynorm = (|y|, 0) and y2b as in split_rows_kernel (y0 = y, no y1), and max |y_il| by
+// integer maximum of the magnitude bits (inf or NaN give inf).  Eight values per lane, two rows
+// in flight per warp.
+__global__ void norms_bf16_kernel(const __nv_bfloat16* __restrict__ y, int64_t ldy, int64_t n, int d,
+                                  float2* __restrict__ ynorm, float2* __restrict__ y2b,
+                                  unsigned int* __restrict__ maxabs_bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float infl = 1.0f + (float)(d + 3) * 1.1920928955078125e-7f;
+  const float defl = 1.0f - (float)(d + 3) * 1.1920928955078125e-7f;
+  const int groups = d / 8;
+  uint32_t mb = 0;
+  for (int64_t r0 = warp; r0 < n; r0 += 2 * nwarps) {
+    float s0[2] = {0.f, 0.f};
+    for (int g = lane; g < groups; g += 32) {
+      uint4 raw[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t row = r0 + q * nwarps;
+        raw[q] = row < n ? __ldg(reinterpret_cast<const uint4*>(y + row * ldy + 8 * g)) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint32_t w[4] = {raw[q].x, raw[q].y, raw[q].z, raw[q].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float lo = __uint_as_float(w[i] << 16), hi = __uint_as_float(w[i] & 0xFFFF0000u);
+          s0[q] = fmaf(lo, lo, fmaf(hi, hi, s0[q]));
+          mb = max(mb, max(w[i] & 0x7FFFu, (w[i] >> 16) & 0x7FFFu));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      for (int off = 16; off > 0; off >>= 1) s0[q] += __shfl_xor_sync(0xffffffffu, s0[q], off);
+      const int64_t row = r0 + q * nwarps;
+      if (lane == 0 && row < n) {
+        ynorm[row] = make_float2(__fsqrt_ru(__fmul_ru(s0[q], infl)), 0.0f);
+        y2b[row] = make_float2(__fmul_rd(s0[q], defl), __fmul_ru(s0[q], infl));
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+  const float mx = mb >= 0x7F80u ? INFINITY : __uint_as_float(mb << 16);
   if (lane == 0) atomicMax(maxabs_bits, __float_as_uint(mx));
 }
 
@@ -625,6 +811,102 @@ __global__ void split_centroids_kernel(const double* __restrict__ c64, int k, in
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     cn2[j] = (float)t;
     atomicMax(cmax_bits, __float_as_uint(__double2float_ru(sqrt(t) * (1.0 + 1e-12))));
+  }
+}
+
+// Hamerly's test after an update: u <- u + delta_a, l <- l - max_{j != a} delta_j (directed
+// rounding; delta_j = st.cmove, the float64 movement of centroid j rounded up).  A row with
+// u < l keeps its bounds and is skipped; the others are appended to sel (counters[3]), in row
+// order within each block of kSelBlock rows (one atomic per block, not per warp: the counter
+// is a single address).  k <= 256.
+constexpr int kSelBlock = 1024;
+__global__ void __launch_bounds__(kSelBlock)
+    bounds_select_kernel(int64_t n, int k, const int32_t* __restrict__ assign, const float* __restrict__ cmove,
+                         float2* __restrict__ bnd, int32_t* __restrict__ sel,
+                         unsigned long long* __restrict__ counters) {
+  __shared__ float mv[kCn2Slots];
+  __shared__ float top2[2];
+  __shared__ int top_j;
+  __shared__ int wcount[kSelBlock / 32];
+  __shared__ unsigned long long blk_base;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) mv[j] = cmove[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m0 = 0.f, m1 = 0.f;
+    int j0 = 0;
+    for (int j = 0; j < k; ++j) {
+      const float v = mv[j];
+      if (v > m0) { m1 = m0; m0 = v; j0 = j; }
+      else if (v > m1) m1 = v;
+    }
+    top2[0] = m0;
+    top2[1] = m1;
+    top_j = j0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * kSelBlock;
+  for (int64_t base = (int64_t)blockIdx.x * kSelBlock; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool eval = false;
+    if (i < n) {
+      const int a = assign[i];
+      float2 b = bnd[i];
+      b.x = __fadd_ru(b.x, mv[a]);
+      b.y = __fsub_rd(b.y, a == top_j ? top2[1] : top2[0]);
+      if (b.x < b.y) bnd[i] = b;
+      else eval = true;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, eval);
+    if (lane == 0) wcount[wid] = __popc(m);
+    __syncthreads();
+    if (wid == 0) {
+      // exclusive scan of the warp counts; one atomic for the block
+      const int c = wcount[lane];
+      int incl = c;
+      for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+      }
+      wcount[lane] = incl - c;
+      if (lane == 31 && incl > 0) blk_base = atomicAdd(counters + 3, (unsigned long long)incl);
+    }
+    __syncthreads();
+    if (eval) sel[blk_base + wcount[wid] + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+    __syncthreads();
+  }
+}
+
+// Rows the next pass evaluates: the selected ones, copied (y0, and y1 for float32 features; from
+// the feature rows themselves when yrow is set) into
+// the compact buffers in sel order when they are at most a fifth of the rows, else every row in
+// place.  Writes counters[2] (rows) and counters[6] (compacted).  One warp per 128-byte chunk.
+__global__ void compact_rows_kernel(int64_t n, int nk, int has_lo, const int32_t* __restrict__ sel,
+                                    const __nv_bfloat16* __restrict__ ys, const __nv_bfloat16* __restrict__ yrow,
+                                    int64_t ldy, __nv_bfloat16* __restrict__ yc,
+                                    unsigned long long* __restrict__ counters) {
+  const unsigned long long cnt = counters[3];
+  const bool compact = cnt * 5 <= (unsigned long long)n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    counters[2] = compact ? cnt : (unsigned long long)n;
+    counters[6] = compact ? 1ull : 0ull;
+  }
+  if (!compact) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int parts = 1 + has_lo;
+  const int64_t total = (int64_t)cnt * nk * parts;
+  const size_t half = (size_t)n * nk * kKC;  // elements of one split part
+  for (int64_t w = warp; w < total; w += nwarps) {
+    const int64_t s = w / (nk * parts);
+    const int rem = (int)(w % (nk * parts));
+    const int part = rem / nk, kc = rem % nk;
+    const int64_t row = sel[s];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(
+        yrow != nullptr ? yrow + row * ldy + (int64_t)kc * kKC : ys + part * half + ((size_t)kc * n + row) * kKC);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(yc + part * half + ((size_t)kc * n + s) * kKC);
+    dst[lane] = __ldcs(src + lane);
   }
 }
 
@@ -660,16 +942,17 @@ bool encode_chunked(CUtensorMap* m, void* ptr, int64_t n, int nk) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 2-D bfloat16 map over rows x dp elements, box 64 x box_rows, 128-byte swizzle.
-bool encode_rows(CUtensorMap* m, void* ptr, int64_t rows, int dp, int box_rows) {
+// 2-D bfloat16 map over rows x dp elements (leading dimension ld), box 64 x box_rows, 128-byte
+// swizzle.
+bool encode_rows(CUtensorMap* m, const void* ptr, int64_t rows, int dp, int box_rows, int64_t ld) {
   EncodeTiled enc = encoder();
   if (enc == nullptr) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -704,26 +987,48 @@ TcPlan kmeans_tc_plan(int64_t n, int k, int d, int y_dtype) {
 
 cudaError_t kmeans_tc_prepare(KmeansState& st, const TcPlan& p, const void* y, int y_dtype, int64_t n,
                               int d, int64_t ldy, unsigned int* maxabs_bits, cudaStream_t s) {
+  // bfloat16 features whose rows are whole 64-element chunks are their own y0: the distance pass
+  // reads them in place through a 2-D map, and only the norms are computed here
+  const bool rowmajor = y_dtype == CSC_BF16 && d % kKC == 0 && rows_vec8(y, d, ldy);
+  st.tc_rowmajor = rowmajor;
   const size_t half = (size_t)n * p.dp * 2;
-  if (!ensure(st.ysplit, half * (1 + p.has_lo)) || !ensure(st.ynorm, (size_t)n * 8) ||
+  if ((!rowmajor && !ensure(st.ysplit, half * (1 + p.has_lo))) || !ensure(st.ynorm, (size_t)n * 8) ||
       !ensure(st.csplit, (size_t)2 * p.npad * p.dp * 2) || !ensure(st.cn2t, (size_t)p.npad * 4) ||
-      !ensure(st.masks, (size_t)n * (p.npad / 16) * 2))
+      !ensure(st.masks, (size_t)n * (p.npad / 16) * 2) || !ensure(st.y2b, (size_t)n * 8) ||
+      !ensure(st.bnd, (size_t)n * 8) || !ensure(st.hsel, (size_t)n * 4) ||
+      !ensure(st.ycomp, half * (1 + p.has_lo)))
     return cudaErrorMemoryAllocation;
-  __nv_bfloat16* y0 = as<__nv_bfloat16>(st.ysplit);
+  __nv_bfloat16* y0 = rowmajor ? nullptr : as<__nv_bfloat16>(st.ysplit);
   __nv_bfloat16* y1 = p.has_lo ? y0 + (size_t)n * p.dp : nullptr;
   const int grid = num_sms() * 8;
-  if (y_dtype == CSC_BF16)
+  if (rowmajor) {
+    norms_bf16_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(y), ldy, n, d, as<float2>(st.ynorm),
+                                           as<float2>(st.y2b), maxabs_bits);
+  } else if (rows_vec8(y, d, ldy)) {
+    if (y_dtype == CSC_BF16)
+      split_rows_vec_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(y), ldy, n, d,
+                                                                p.dp, y0, y1, as<float2>(st.ynorm),
+                                                                as<float2>(st.y2b), maxabs_bits);
+    else
+      split_rows_vec_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(y), ldy, n, d, p.dp, y0, y1,
+                                                        as<float2>(st.ynorm), as<float2>(st.y2b), maxabs_bits);
+  } else if (y_dtype == CSC_BF16)
     split_rows_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(y), ldy, n, d,
-                                                          p.dp, y0, y1, as<float2>(st.ynorm), maxabs_bits);
+                                                          p.dp, y0, y1, as<float2>(st.ynorm),
+                                                          as<float2>(st.y2b), maxabs_bits);
   else
     split_rows_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(y), ldy, n, d, p.dp, y0, y1,
-                                                  as<float2>(st.ynorm), maxabs_bits);
+                                                  as<float2>(st.ynorm), as<float2>(st.y2b), maxabs_bits);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(st.tmaps);
-  if (!encode_chunked(&maps[0], y0, n, p.nk) ||
-      !encode_chunked(&maps[1], p.has_lo ? (void*)y1 : (void*)y0, n, p.nk) ||
-      !encode_rows(&maps[2], st.csplit.ptr, 2 * (int64_t)p.npad, p.dp, p.npad))
+  __nv_bfloat16* c0 = as<__nv_bfloat16>(st.ycomp);
+  __nv_bfloat16* c1 = p.has_lo ? c0 + (size_t)n * p.dp : c0;
+  const bool ymaps = rowmajor ? encode_rows(&maps[0], y, n, d, kTM, ldy) && encode_rows(&maps[1], y, n, d, kTM, ldy)
+                              : encode_chunked(&maps[0], y0, n, p.nk) &&
+                                    encode_chunked(&maps[1], p.has_lo ? (void*)y1 : (void*)y0, n, p.nk);
+  if (!ymaps || !encode_rows(&maps[2], st.csplit.ptr, 2 * (int64_t)p.npad, p.dp, p.npad, p.dp) ||
+      !encode_chunked(&maps[3], c0, n, p.nk) || !encode_chunked(&maps[4], c1, n, p.nk))
     return cudaErrorInvalidValue;
   const void* fn = p.nv == 16   ? (const void*)kmeans_tc_kernel<16>
                    : p.nv == 32 ? (const void*)kmeans_tc_kernel<32>
@@ -733,10 +1038,21 @@ cudaError_t kmeans_tc_prepare(KmeansState& st, const TcPlan& p, const void* y, i
 }
 
 cudaError_t kmeans_tc_pass(KmeansState& st, const TcPlan& p, const void* y, int y_dtype, int64_t n, int d,
-                           int64_t ldy, int k, int track, cudaStream_t s) {
+                           int64_t ldy, int k, int track, bool select, cudaStream_t s) {
   unsigned int* cmax_bits = as<unsigned int>(st.bits) + 3;
   cudaError_t e = cudaMemsetAsync(cmax_bits, 0, 4, s);
   if (e != cudaSuccess) return e;
+  unsigned long long* counters = as<unsigned long long>(st.counters);
+  if (select) {
+    const int64_t blocks = std::min<int64_t>((n + kSelBlock - 1) / kSelBlock, (int64_t)num_sms() * 2);
+    bounds_select_kernel<<<(int)blocks, kSelBlock, 0, s>>>(n, k, as<int32_t>(st.assign), as<float>(st.cmove),
+                                                     as<float2>(st.bnd), as<int32_t>(st.hsel), counters);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    compact_rows_kernel<<<num_sms() * 8, 256, 0, s>>>(
+        n, p.nk, p.has_lo, as<int32_t>(st.hsel), as<__nv_bfloat16>(st.ysplit),
+        st.tc_rowmajor ? static_cast<const __nv_bfloat16*>(y) : nullptr, ldy, as<__nv_bfloat16>(st.ycomp), counters);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   split_centroids_kernel<<<p.npad, 128, 0, s>>>(as<double>(st.c64), k, d, p.npad, p.dp,
                                                   as<__nv_bfloat16>(st.csplit), as<float>(st.cn2t), cmax_bits);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -760,15 +1076,19 @@ cudaError_t kmeans_tc_pass(KmeansState& st, const TcPlan& p, const void* y, int 
   a.flagged = as<int32_t>(st.flagged);
   a.masks = as<uint16_t>(st.masks);
   a.moved = as<int32_t>(st.moved);
-  a.counters = as<unsigned long long>(st.counters);
+  a.counters = counters;
+  a.sel = select ? as<int32_t>(st.hsel) : nullptr;
+  a.rowmajor = st.tc_rowmajor;
+  a.y2b = as<float2>(st.y2b);
+  a.bnd = as<float2>(st.bnd);
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(st.tmaps);
   const int64_t ntiles = (n + kTM - 1) / kTM;
   const int grid = (int)std::min<int64_t>(num_sms(), ntiles);
   switch (p.nv) {
-    case 16: kmeans_tc_kernel<16><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], a); break;
-    case 32: kmeans_tc_kernel<32><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], a); break;
-    case 64: kmeans_tc_kernel<64><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], a); break;
-    default: kmeans_tc_kernel<128><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], a); break;
+    case 16: kmeans_tc_kernel<16><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a); break;
+    case 32: kmeans_tc_kernel<32><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a); break;
+    case 64: kmeans_tc_kernel<64><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a); break;
+    default: kmeans_tc_kernel<128><<<grid, kThreads, p.smem, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a); break;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the float32 centroids, their norms and max |c32| come from the last finalize
@@ -790,6 +1110,10 @@ void kmeans_tc_release(KmeansState& st) {
   release(st.csplit);
   release(st.cn2t);
   release(st.masks);
+  release(st.y2b);
+  release(st.bnd);
+  release(st.hsel);
+  release(st.ycomp);
 }
 
 }  // namespace csc

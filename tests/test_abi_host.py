@@ -37,7 +37,7 @@ def test_header_symbols_exported(lib):
     assert not missing, missing
     # the binding declares exactly the header's entry points
     assert sorted(_abi.SIGNATURES) == names
-    assert lib.csc_abi_version() == 7
+    assert lib.csc_abi_version() == 8
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -345,6 +345,33 @@ def test_kmeans_exact_ties_lowest_index(gpu_lib):
     np.testing.assert_array_equal(out["assign"], lab_ref)
 
 
+@pytest.mark.parametrize("bf16", [False, True])
+def test_kmeans_bound_skipping_is_exact(gpu_lib, bf16):
+    """Hamerly skipping on the tensor-core pass, on overlapping clusters that take many Lloyd
+    passes: the assignment, the pass count and the centroids equal the oracle's plain Lloyd
+    (Section 2.1, Eq. 1), and the passes after the first evaluate fewer than all rows
+    (csc_stats.kmeans_rows)."""
+    n, d, k = 60000, 64, 40
+    y, _ = W.clustered_points(n, d, k, seed=21, spread=1.2)
+    idx = W.forgy_indices(n, k, seed=22)
+    if bf16:
+        yt = torch.from_numpy(y).to(torch.bfloat16)
+        y = yt.float().numpy()
+    else:
+        yt = torch.from_numpy(y)
+    lab_ref, c_ref, it_ref, _ = km.lloyd(y.astype(np.float64), km.forgy_centroids(y, idx), max_iter=100)
+    with gpu_lib.Context() as ctx:
+        out = ctx.kmeans(yt.cuda(), k, idx, max_iter=100,
+                         assign_out=torch.zeros(n, dtype=torch.int32, device="cuda"))
+        st = ctx.stats()
+    np.testing.assert_array_equal(out["assign"].cpu().numpy(), lab_ref)
+    assert out["iters"] == it_ref and it_ref >= 10
+    np.testing.assert_allclose(out["centroids"], c_ref, rtol=0, atol=1e-12)
+    assert st["kmeans_passes"] == it_ref
+    print(f"passes {it_ref}, rows evaluated {st['kmeans_rows']} of {it_ref * n}")
+    assert n <= st["kmeans_rows"] < 0.6 * it_ref * n
+
+
 @pytest.mark.parametrize("reorder", [1, 0, 2])
 def test_algorithm1_dynamic_parity_cfg1(gpu_lib, cfg1_graph, reorder):
     """SBM n=2000, k=10, degree 20, d=64, m=50, 1% rewiring per step, p=0.5: 1 + 5 snapshots."""
