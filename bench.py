@@ -329,9 +329,11 @@ def batched_comparison(seed=77, count=512, m=60):
 
 
 def differentiation_timing(seed=4, reps=3):
-    """Forward (with checkpoints every ceil(sqrt m) steps), loss gradient and vector-Jacobian
-    product of the k-means loss of the filtered features, at the differentiation workload's
-    size: SBM n = 2e5, k = 20, degree 25, d = 128, m = 60, unit weights, float32."""
+    """Forward, loss gradient and vector-Jacobian product of the k-means loss of the filtered
+    features, at the differentiation workload's size: SBM n = 2e5, k = 20, degree 25, d = 128,
+    m = 60, unit weights, float32.  Two checkpoint plans: every step kept (stride 1, 6.1 GB at
+    this size, nothing recomputed) and every ceil(sqrt m) = 8 steps (the backward pass
+    recomputes each segment)."""
     import numpy as np
     import torch
 
@@ -346,31 +348,33 @@ def differentiation_timing(seed=4, reps=3):
     a = csc.csc_filter_coeffs(m, 0.3)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    with csc.Context() as ctx:
-        ctx.set_graph(g.n, torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda())
-        psi = torch.zeros((g.n, c), device="cuda")
-        gpsi = torch.zeros_like(psi)
-        gw = torch.zeros(g.col_idx.size, device="cuda")
-        t = [0.0, 0.0, 0.0]
-        for rep in range(reps + 1):
-            torch.cuda.synchronize()
-            ev[0].record(stream)
-            ctx.filter_forward(m, a, r, psi, 0)
-            ev[1].record(stream)
-            ctx.kmeans_loss_grad(psi, mu, assign, gpsi)
-            ev[2].record(stream)
-            ctx.filter_vjp(gpsi, gw)
-            ev[3].record(stream)
-            torch.cuda.synchronize()
-            if rep > 0:
-                for i in range(3):
-                    t[i] += ev[i].elapsed_time(ev[i + 1]) / reps
     units = float(g.nnz) * c * m
-    return {"workload": f"SBM n={n}, k={k}, degree 25, d={c}, m={m}, unit weights, fp32, "
-                        "checkpoints every 8 steps", "nnz": int(g.nnz),
-            "forward_ms": t[0], "loss_grad_ms": t[1], "vjp_ms": t[2],
-            "backward_over_forward": t[2] / t[0], "forward_rate": units / (t[0] / 1e3),
-            "unit": UNIT}
+    out = {"workload": f"SBM n={n}, k={k}, degree 25, d={c}, m={m}, unit weights, fp32", "nnz": int(g.nnz),
+           "unit": UNIT}
+    for name, stride in (("every_step_kept", 1), ("checkpoints_every_8", 0)):
+        with csc.Context() as ctx:
+            ctx.set_graph(g.n, torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda())
+            psi = torch.zeros((g.n, c), device="cuda")
+            gpsi = torch.zeros_like(psi)
+            gw = torch.zeros(g.col_idx.size, device="cuda")
+            t = [0.0, 0.0, 0.0]
+            for rep in range(reps + 1):
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                ctx.filter_forward(m, a, r, psi, stride)
+                ev[1].record(stream)
+                ctx.kmeans_loss_grad(psi, mu, assign, gpsi)
+                ev[2].record(stream)
+                ctx.filter_vjp(gpsi, gw)
+                ev[3].record(stream)
+                torch.cuda.synchronize()
+                if rep > 0:
+                    for i in range(3):
+                        t[i] += ev[i].elapsed_time(ev[i + 1]) / reps
+        out[name] = {"forward_ms": t[0], "loss_grad_ms": t[1], "vjp_ms": t[2],
+                     "backward_over_forward": t[2] / t[0], "forward_rate": units / (t[0] / 1e3)}
+    out["backward_over_forward"] = out["every_step_kept"]["backward_over_forward"]
+    return out
 
 
 def compressive_timing(ctx, full_assign, planted, k, n, seed=11, reps=3):

@@ -19,7 +19,9 @@
 // The forward pass keeps the pair (V_{ks-1}, V_{ks}) for every segment k of `stride` steps;
 // the backward pass walks the segments in reverse, recomputes each from its pair, and runs
 // one fused kernel per step: the adjoint step, the per-edge update of H (gathering V_j and
-// Phi_{j+1} of the neighbours) and the partial sums of <G, T_j R>.
+// Phi_{j+1} of the neighbours) and the partial sums of <G, T_j R>.  With stride 1 the forward
+// pass writes every V_j straight into its checkpoint slot and the backward pass reads them
+// there: nothing is copied or recomputed.
 #include <algorithm>
 #include <cmath>
 
@@ -473,14 +475,17 @@ extern "C" csc_status csc_filter_forward(csc_ctx* ctx, int m, const double* coef
     G_CUDA(csc::launch_copy_tile(gs.rt.ptr, R, CSC_F32, n, w, ldr, c0, valid, s, csc::to_caller(ctx)));
     G_CUDA(cudaMemsetAsync(psi_tile, 0, blk * 4, s));
     float* tile_ck = ck + (size_t)tile * gs.slots * blk;
-    auto vp = [&](int j) { return csc::as<float>(ctx->tbuf[j % 3]); };  // V_j lives in tbuf[j % 3]
+    // V_j lives in tbuf[j % 3], or in its checkpoint slot j - 1 when every step is kept
+    auto vp = [&](int j) {
+      return gs.stride == 1 ? tile_ck + (size_t)(j - 1) * blk : csc::as<float>(ctx->tbuf[j % 3]);
+    };
     for (int j = 0; j < m; ++j) {
       csc_status st = csc::forward_steps(ctx, j, j + 1, vp, psi_tile, w, part, grid, s);
       if (st != CSC_OK) return st;
+      if (gs.stride == 1) continue;
       const int v = j + 1;  // V_v was just produced
       int slot = -1;
-      if (gs.stride == 1) slot = v - 1;
-      else if (v % gs.stride == 0 && v < m) slot = 2 * (v / gs.stride - 1) + 1;
+      if (v % gs.stride == 0 && v < m) slot = 2 * (v / gs.stride - 1) + 1;
       else if ((v + 1) % gs.stride == 0 && v + 1 < m) slot = 2 * ((v + 1) / gs.stride - 1);
       if (slot >= 0)
         G_CUDA(cudaMemcpyAsync(tile_ck + (size_t)slot * blk, vp(v), blk * 4, cudaMemcpyDeviceToDevice, s));
@@ -505,7 +510,7 @@ extern "C" csc_status csc_filter_vjp(csc_ctx* ctx, const float* grad_psi, int64_
   const int sms = csc::num_sms();
   const int agrid = sms * 8;
   G_ALLOC(csc::ensure(gs.gt, blk * 4));
-  G_ALLOC(csc::ensure(gs.seg, (size_t)(S + 2) * blk * 4));
+  if (S > 1) G_ALLOC(csc::ensure(gs.seg, (size_t)(S + 2) * blk * 4));
   for (auto& b : gs.phi) G_ALLOC(csc::ensure(b, blk * 4));
   G_ALLOC(csc::ensure(gs.H, (size_t)std::max<int64_t>(nnz, 1) * 4));
   G_ALLOC(csc::ensure(gs.part, csc::part_doubles(std::max(grid, agrid)) * 8));
@@ -522,20 +527,18 @@ extern "C" csc_status csc_filter_vjp(csc_ctx* ctx, const float* grad_psi, int64_
     G_CUDA(csc::launch_copy_tile(gs.rt.ptr, gs.R, CSC_F32, n, w, gs.ldr, c0, valid, s, csc::to_caller(ctx)));
     G_CUDA(csc::launch_copy_tile(gs.gt.ptr, grad_psi, CSC_F32, n, w, ldg, c0, valid, s, csc::to_caller(ctx)));
     const float* tile_ck = ck + (size_t)tile * gs.slots * blk;
-    // V_j of the current segment [lo, hi]: seg slot j - lo + 1 (slot 0 holds V_{lo-1})
+    // V_j (j >= 1) of the current segment [lo, hi]: its checkpoint slot j - 1 when every step
+    // is kept, else seg slot j - lo + 1 (slot 0 holds V_{lo-1})
     int lo = 0, hi = 0;
-    auto vseg = [&](int j) { return seg + (size_t)(j - lo + 1) * blk; };
+    auto vseg = [&](int j) -> float* {
+      return S == 1 ? const_cast<float*>(tile_ck) + (size_t)(j - 1) * blk : seg + (size_t)(j - lo + 1) * blk;
+    };
     auto phi = [&](int j) { return csc::as<float>(gs.phi[((j % 3) + 3) % 3]); };
     for (int k = gs.segs - 1; k >= 0; --k) {
       lo = k * S;
       hi = std::min(m, lo + S);
       // recompute V_{lo+1} .. V_hi (V_lo and V_{lo-1} from the checkpoints, or from R)
-      if (S == 1) {
-        // every V_j is a checkpoint: slot v - 1 holds V_v
-        if (lo >= 1) G_CUDA(cudaMemcpyAsync(vseg(lo), tile_ck + (size_t)(lo - 1) * blk, blk * 4, cudaMemcpyDeviceToDevice, s));
-        if (lo >= 2) G_CUDA(cudaMemcpyAsync(vseg(lo - 1), tile_ck + (size_t)(lo - 2) * blk, blk * 4, cudaMemcpyDeviceToDevice, s));
-        G_CUDA(cudaMemcpyAsync(vseg(hi), tile_ck + (size_t)(hi - 1) * blk, blk * 4, cudaMemcpyDeviceToDevice, s));
-      } else {
+      if (S > 1) {
         if (k >= 1) {
           G_CUDA(cudaMemcpyAsync(vseg(lo - 1), tile_ck + (size_t)(2 * (k - 1)) * blk, blk * 4, cudaMemcpyDeviceToDevice, s));
           G_CUDA(cudaMemcpyAsync(vseg(lo), tile_ck + (size_t)(2 * (k - 1) + 1) * blk, blk * 4, cudaMemcpyDeviceToDevice, s));

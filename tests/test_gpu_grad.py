@@ -60,7 +60,7 @@ def gpu_grads(gpu_lib, g, w, r, a, mu, assign, stride, reorder=1):
         return psi.cpu().numpy(), loss, gpsi.cpu().numpy(), ga, gw.cpu().numpy()
 
 
-@pytest.mark.parametrize("c,stride,reorder", [(16, 0, 1), (16, 1, 1), (130, 7, 1), (16, 0, 0)])
+@pytest.mark.parametrize("c,stride,reorder", [(16, 0, 1), (16, 1, 1), (130, 7, 1), (16, 0, 0), (40, 16, 1), (64, 1, 0)])
 def test_gradients_match_oracle_and_finite_differences(gpu_lib, c, stride, reorder):
     g, w, r, a, mu, assign = small_case(c)
     psi, loss, gpsi, ga, gw = gpu_grads(gpu_lib, g, w, r, a, mu, assign, stride, reorder)
