@@ -301,7 +301,7 @@ struct KmeansState {
   alignas(64) unsigned char tmaps[5][128];  // TMA maps of y0, y1, (c0, c1), compacted y0, y1
   unsigned long long* hist_host = nullptr;   // pinned [passes][5]: counters of each pass
   size_t hist_cap = 0;
-  cudaEvent_t pass_ev[2] = {nullptr, nullptr};  // completion of a pass's counter copy
+  cudaEvent_t pass_ev[3] = {nullptr, nullptr, nullptr};  // completion of a pass's counter copy
 };
 
 // Shape of the tensor-core distance pass for (n, k, d, dtype); ok = false when k or d

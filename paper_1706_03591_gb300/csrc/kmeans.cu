@@ -1211,13 +1211,16 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
   if (use_tc) {
     // Tensor-core distance pass (every row in the first pass; later passes skip the rows whose
     // Hamerly bounds certify their centroid); near ties decided in float64.  The
-    // host queues pass it before it reads the counters of pass it - 1 (copied to pinned
-    // memory), so the GPU does not wait for the host between passes.  The update after pass
+    // host queues pass it before it reads the counters of pass it - kPassLag (copied to pinned
+    // memory), so the GPU does not wait for the host between passes.  A lag of 2 would also
+    // cover a host slower than a pass, but its second update is then always the full
+    // recomputation (2.5 ms more per call on the 8e6-node power-law features), so it is 1.  The update after pass
     // it is either the full recomputation or the incremental one from the moved rows; both
     // give the same integer sums, and the choice (full after the first pass and whenever the
     // previous pass moved more than n / 16 rows) only affects speed.  When pass j turns out
-    // to have converged, pass j + 1 is already queued: it finds no move and leaves the
-    // assignment, the sums and the centroids as they were, so the result is the one at j.
+    // to have converged, passes j + 1 .. j + kPassLag are already queued: they find no move and
+    // leave the assignment, the sums and the centroids as they were, so the result is the one
+    // at j.
     if (st.hist_cap < (size_t)max_iter * 5) {
       if (st.hist_host) cudaFreeHost(st.hist_host);
       st.hist_host = nullptr;
@@ -1233,6 +1236,7 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     // bound selection per pass; it stops while it does not pay (the last examined selecting pass
     // evaluated every row in place) and is tried again every kSelectRetry passes
     constexpr int kSelectRetry = 4;
+    constexpr int kPassLag = 1, kPassLag1 = kPassLag + 1;  // passes queued ahead of the host
     std::vector<char> selected((size_t)max_iter + 2, 0);
     bool select_paid = true;
     int last_select = 0;
@@ -1240,7 +1244,7 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
     int64_t decided = 0;
     // reads the counters of pass j (1-based) once its copy has completed
     auto examine = [&](int j) -> csc_status {
-      cudaError_t e = cudaEventSynchronize(st.pass_ev[j & 1]);
+      cudaError_t e = cudaEventSynchronize(st.pass_ev[j % kPassLag1]);
       if (e != cudaSuccess) {
         if (err) *err = std::string("k-means: ") + cudaGetErrorString(e);
         return CSC_ECUDA;
@@ -1275,10 +1279,10 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
       CK(kmeans_tc_pass(st, tp, y, y_dtype, n, d, ldy, k, it > 1 || prev_assign != nullptr, sel, s));
       launches += 3;
       CK(cudaMemcpyAsync(st.hist_host + (size_t)(it - 1) * 5, counters, 40, cudaMemcpyDeviceToHost, s));
-      CK(cudaEventRecord(st.pass_ev[it & 1], s));
+      CK(cudaEventRecord(st.pass_ev[it % kPassLag1], s));
       stop = it;
-      if (it > 1) {
-        const csc_status cs = examine(it - 1);
+      if (it > kPassLag) {
+        const csc_status cs = examine(it - kPassLag);
         if (cs != CSC_OK) return cs;
         if (converged) break;
       }
@@ -1293,8 +1297,8 @@ csc_status run_typed(KmeansState& st, const TY* y, int64_t n, int d, int64_t ldy
       }
       CK(finalize());
     }
-    if (!converged) {
-      const csc_status cs = examine(stop);
+    for (int j = examined + 1; j <= stop && !converged; ++j) {
+      const csc_status cs = examine(j);
       if (cs != CSC_OK) return cs;
     }
     res->iters = examined;
