@@ -218,9 +218,9 @@ int plan_columns(const std::vector<int>& plan) {
   return t;
 }
 
-// Algorithmic bytes of one general step launch over a tile of width w (SURVEY-style forward form):
-// col_idx (+ weights), row_ptr, D^-1/2, V_{j-1} (s_prev bytes per value), V_j once, V_{j+1}, and Psi
-// read and write.
+// Algorithmic bytes of one general step launch over a tile of width w, each array counted
+// once: col_idx (+ weights), row_ptr, D^-1/2, V_{j-1} (s_prev bytes per value), V_j, V_{j+1},
+// and Psi read and write.
 double step_launch_bytes(int64_t n, int64_t nnz, bool weighted, int w, int s_prev) {
   return 4.0 * nnz * (weighted ? 2 : 1) + 8.0 * (n + 1) + 4.0 * n + (double)n * w * (s_prev + 4 + 4 + 8);
 }
