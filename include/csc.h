@@ -373,9 +373,10 @@ csc_status csc_cheb_filter_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
 /* Psi = sum_{j=0}^{m} coef[j] T_j(L~) R on the context's graph (its edge weights, unit if
  * none) for an arbitrary coefficient vector (host double[m+1]) and the caller's signal block R
  * (device float32, n x c, leading dimension ldr), written to psi_out (device float32, n x c,
- * leading dimension ldp).  The recursion state at every stride-th step (stride 0: ceil(sqrt m);
- * 1: every step, no recomputation later) and a copy of R are kept in the context for
- * csc_filter_vjp.  Errors: CSC_ESTATE without a graph, CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA. */
+ * leading dimension ldp).  The recursion state at every stride-th step (stride 0: ceil(sqrt m),
+ * about 2 n c sqrt(m) floats; 1: every step, m n c floats written in place, and csc_filter_vjp
+ * recomputes nothing) and a copy of R are kept in the context for csc_filter_vjp.
+ * Errors: CSC_ESTATE without a graph, CSC_EINVAL, CSC_ENOMEM, CSC_ECUDA. */
 csc_status csc_filter_forward(csc_ctx* ctx, int m, const double* coef, const float* R, int c,
                               int64_t ldr, float* psi_out, int64_t ldp, int stride);
 
