@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define CSC_ABI_VERSION 8
+#define CSC_ABI_VERSION 9
 
 typedef struct csc_ctx csc_ctx;
 
@@ -122,6 +122,19 @@ void csc_default_opts(csc_opts* opts);
 const char* csc_status_string(csc_status s);
 /* CSC_ABI_VERSION of the built library. */
 int csc_abi_version(void);
+
+/* Host only.  The column tiles of a filtering pass over c columns (Section 3.3's recursion, run
+ * tile by tile): widths in {8, 16, 32, 64} covering c that minimise sum (8 + w) over the tiles,
+ * widest first (ties keep fewer, wider tiles); col_tile > 0 (8, 16, 32, 64 or 128) forces that
+ * width.  Writes up to cap widths to widths_out and returns the number of tiles; -1 for bad
+ * arguments, -(tiles + 1) when cap is too small. */
+int csc_tile_plan(int c, int col_tile, int* widths_out, int cap);
+
+/* Host only.  Algorithmic bytes of one general Chebyshev step launch over a tile of width w:
+ * 4 nnz (8 nnz when weighted) + 8 (n + 1) + 4 n + n w (s_prev + 4 + 4 + 8), i.e. the column
+ * indices (and weights), row offsets and D^-1/2 once, V_{j-1} (s_prev bytes per value), V_j,
+ * V_{j+1}, and Psi read and written (the per-launch term of csc_stats.step_bytes). */
+double csc_step_launch_bytes(int64_t n, int64_t nnz, int weighted, int w, int s_prev);
 
 /* Creates a context on the current CUDA device.  `cuda_stream` is a cudaStream_t
  * (NULL = default stream).  opts may be NULL (defaults).  *out is owned by the

@@ -23,7 +23,7 @@ __all__ = [
     "csc_abi_version", "csc_get_stats", "csc_cheb_filter_noalloc", "csc_filter_batched",
     "csc_filter_forward", "csc_filter_vjp", "csc_kmeans_loss_grad", "cheb_filter_layer",
     "csc_laplacian_distance", "csc_compressive_cluster", "csc_save_state", "csc_load_state",
-    "csc_splice", "csc_reuse_policy", "csc_filter_adaptive",
+    "csc_splice", "csc_reuse_policy", "csc_filter_adaptive", "csc_tile_plan", "csc_step_launch_bytes",
 ]
 
 
@@ -151,6 +151,21 @@ def csc_filter_coeffs(m: int, lambda_c: float) -> np.ndarray:
 
 def csc_count_tolerance(k: int, c: int) -> float:
     return _lib().csc_count_tolerance(k, c)
+
+
+def csc_tile_plan(c: int, col_tile: int = 0) -> list:
+    """Widths of the column tiles of a filtering pass over c columns (host only)."""
+    cap = max(1, c // 8 + 1)
+    out = (C.c_int * cap)()
+    t = _lib().csc_tile_plan(int(c), int(col_tile), out, cap)
+    if t < 0:
+        raise ValueError(f"csc_tile_plan: bad arguments (c={c}, col_tile={col_tile})")
+    return [int(out[i]) for i in range(t)]
+
+
+def csc_step_launch_bytes(n: int, nnz: int, weighted: bool, w: int, s_prev: int = 4) -> float:
+    """Algorithmic bytes of one general step launch over a tile of width w (host only)."""
+    return float(_lib().csc_step_launch_bytes(int(n), int(nnz), int(bool(weighted)), int(w), int(s_prev)))
 
 
 def csc_count_from_moments(m: int, mu, lambda_c: float, d: int, c: int) -> float:

@@ -77,6 +77,8 @@ SIGNATURES = {
     "csc_default_opts": (None, [C.POINTER(csc_opts)]),
     "csc_status_string": (C.c_char_p, [_i32]),
     "csc_abi_version": (_i32, []),
+    "csc_tile_plan": (_i32, [_i32, _i32, C.POINTER(C.c_int), _i32]),
+    "csc_step_launch_bytes": (C.c_double, [C.c_int64, C.c_int64, _i32, _i32, _i32]),
     "csc_create": (_i32, [C.POINTER(_p), C.POINTER(csc_opts), _p]),
     "csc_destroy": (None, [_p]),
     "csc_last_error": (C.c_char_p, [_p]),

@@ -195,8 +195,9 @@ csc_status fail(csc_ctx* ctx, csc_status s, const std::string& msg) {
 // the SBM at n = 1e6 0.30, 0.53 and 0.96 ms at w = 16, 32 and 64, so wide tiles are cheaper per
 // column on both, and a small remainder takes its own narrow tile.  col_tile > 0 forces one width.
 constexpr int kTileFixed = 8;
-std::vector<int> tile_plan(const csc_ctx* ctx, int c) {
-  if (ctx->opts.col_tile > 0) return std::vector<int>((c + ctx->opts.col_tile - 1) / ctx->opts.col_tile, ctx->opts.col_tile);
+std::vector<int> plan_tiles(int c, int col_tile) {
+  if (c <= 0) return {};
+  if (col_tile > 0) return std::vector<int>((c + col_tile - 1) / col_tile, col_tile);
   static const int widths[4] = {64, 32, 16, 8};
   std::vector<int> cost(c + 1, 0), pick(c + 1, 8);
   for (int r = 1; r <= c; ++r) {
@@ -211,6 +212,7 @@ std::vector<int> tile_plan(const csc_ctx* ctx, int c) {
   std::sort(plan.begin(), plan.end(), [](int x, int y) { return x > y; });
   return plan;
 }
+std::vector<int> tile_plan(const csc_ctx* ctx, int c) { return plan_tiles(c, ctx->opts.col_tile); }
 
 int plan_columns(const std::vector<int>& plan) {
   int t = 0;
@@ -531,6 +533,18 @@ const char* csc_status_string(csc_status s) {
 }
 
 int csc_abi_version(void) { return CSC_ABI_VERSION; }
+
+int csc_tile_plan(int c, int col_tile, int* widths_out, int cap) {
+  if (c < 0 || (col_tile != 0 && !valid_tile(col_tile)) || (cap > 0 && !widths_out)) return -1;
+  const std::vector<int> plan = plan_tiles(c, col_tile);
+  if ((int)plan.size() > cap) return -(int)plan.size() - 1;
+  for (size_t i = 0; i < plan.size(); ++i) widths_out[i] = plan[i];
+  return (int)plan.size();
+}
+
+double csc_step_launch_bytes(int64_t n, int64_t nnz, int weighted, int w, int s_prev) {
+  return step_launch_bytes(n, nnz, weighted != 0, w, s_prev);
+}
 
 csc_status csc_create(csc_ctx** out, const csc_opts* opts, void* cuda_stream) {
   if (!out) return CSC_EINVAL;

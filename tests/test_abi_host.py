@@ -37,7 +37,7 @@ def test_header_symbols_exported(lib):
     assert not missing, missing
     # the binding declares exactly the header's entry points
     assert sorted(_abi.SIGNATURES) == names
-    assert lib.csc_abi_version() == 8
+    assert lib.csc_abi_version() == 9
 
 
 def test_missing_library_fails_loudly(tmp_path):
@@ -143,3 +143,40 @@ def test_similarity_policy_matches_oracle(lib):
             reuse_policy(d, p_max, rho, alpha, budget, rho_skip, since)
     with pytest.raises(lib.CscError):
         lib.csc_reuse_policy(10, 0.5, 1.0, 0.0, 1.0, 0.0)  # alpha must be positive with a budget
+
+
+def test_tile_plan_minimises_its_cost_model():
+    """The column tiles of a pass (csc_tile_plan): widths in {8, 16, 32, 64}, widest first,
+    covering c, with the least sum (8 + w); against exhaustive search over tile counts."""
+    import paper_1706_03591_gb300 as csc
+
+    def best(c):
+        top = c // 8 + 2
+        return min(8 * (a + b + e + f) + 64 * a + 32 * b + 16 * e + 8 * f
+                   for a in range(top // 8 + 2) for b in range(3) for e in range(3) for f in range(3)
+                   if 64 * a + 32 * b + 16 * e + 8 * f >= c)
+
+    for c in range(1, 260):
+        plan = csc.csc_tile_plan(c)
+        assert plan == sorted(plan, reverse=True)
+        assert set(plan) <= {8, 16, 32, 64}
+        assert sum(plan) >= c and sum(plan) - min(plan) < c  # no tile is idle
+        assert sum(8 + w for w in plan) == best(c), c
+    assert csc.csc_tile_plan(39) == [32, 8]
+    assert csc.csc_tile_plan(64) == [64]
+    assert csc.csc_tile_plan(100) == [64, 32, 8]
+    assert csc.csc_tile_plan(0) == []
+    assert csc.csc_tile_plan(39, 16) == [16, 16, 16]
+    assert csc.csc_tile_plan(130, 128) == [128, 128]
+    with pytest.raises(ValueError):
+        csc.csc_tile_plan(10, 12)
+
+
+def test_step_launch_bytes():
+    """Algorithmic bytes of a step launch: indices (and weights), offsets and D^-1/2 once, then
+    per row and column V_{j-1} (s_prev bytes), V_j, V_{j+1} and Psi read and written."""
+    import paper_1706_03591_gb300 as csc
+    n, nnz = 8_000_000, 198_173_034
+    assert csc.csc_step_launch_bytes(n, nnz, False, 32) == 4 * nnz + 8 * (n + 1) + 4 * n + n * 32 * 20
+    assert csc.csc_step_launch_bytes(n, nnz, True, 8) == 8 * nnz + 8 * (n + 1) + 4 * n + n * 8 * 20
+    assert csc.csc_step_launch_bytes(1000, 0, False, 64, 2) == 8 * 1001 + 4 * 1000 + 1000 * 64 * 18
